@@ -1,0 +1,136 @@
+"""CPU oracle for the LCS table - TEST INFRASTRUCTURE ONLY.
+
+Only `tests/`, `__graft_entry__.smoke()` and the CPU-baseline leg of
+`bench.py` may import this package.  The product library never calls it and
+shares no code with it; it is built with plain gcc from `lcs_oracle.c`.
+
+Functions (all follow Eq. (1) of the paper's Sec. "PACO LCS", generalised to
+caller-given first row/column, see `lcs_oracle.c`):
+
+* `lcs(a, b, top=None, left=None)` -> (L, bottom_row[m+1], right_col[n+1])
+* `lcs_table(a, b, top=None, left=None)` -> full (n+1) x (m+1) table
+* `lcs_batch(a_cat, a_off, b_cat, b_off, threads)` -> per-pair L, rows, cols
+
+Pins that tie it to something other than itself live in
+`tests/test_oracle_pins.py` (brute-force enumeration, indel distance,
+closed forms, invariants, the CLRS worked example).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "lcs_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain C, -O2, no vector intrinsics)."""
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-pthread",
+                               _SRC, "-o", tmp])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB_PATH)
+            P = ctypes.c_void_p
+            I64 = ctypes.c_int64
+            lib.oracle_lcs.argtypes = [P, I64, P, I64, P, P, P, P, P]
+            lib.oracle_lcs.restype = ctypes.c_int
+            lib.oracle_lcs_table.argtypes = [P, I64, P, I64, P, P, P]
+            lib.oracle_lcs_table.restype = ctypes.c_int
+            lib.oracle_lcs_batch.argtypes = [P, P, P, P, I64, P, P, P, P, P, ctypes.c_int]
+            lib.oracle_lcs_batch.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _ptr(x):
+    return None if x is None else x.ctypes.data_as(ctypes.c_void_p)
+
+
+def _u8(x):
+    if isinstance(x, (bytes, bytearray)):
+        return np.frombuffer(bytes(x), dtype=np.uint8).copy()
+    return np.ascontiguousarray(np.asarray(x, dtype=np.uint8))
+
+
+def _i32(x):
+    return None if x is None else np.ascontiguousarray(np.asarray(x, dtype=np.int32))
+
+
+def lcs(a, b, top=None, left=None):
+    """(L, bottom_row, right_col) of the table of Eq. (1) with optional
+    first row `top` (m+1 values) and first column `left` (n+1 values)."""
+    lib = _load()
+    a = _u8(a)
+    b = _u8(b)
+    n, m = a.size, b.size
+    top = _i32(top)
+    left = _i32(left)
+    if top is not None and top.size != m + 1:
+        raise ValueError("top must have m+1 entries")
+    if left is not None and left.size != n + 1:
+        raise ValueError("left must have n+1 entries")
+    row = np.empty(m + 1, dtype=np.int32)
+    col = np.empty(n + 1, dtype=np.int32)
+    L = ctypes.c_int32(0)
+    rc = lib.oracle_lcs(_ptr(a), n, _ptr(b), m, _ptr(top), _ptr(left), _ptr(row), _ptr(col),
+                        ctypes.byref(L))
+    if rc != 0:
+        raise ValueError(f"oracle_lcs failed ({rc})")
+    return int(L.value), row, col
+
+
+def lcs_table(a, b, top=None, left=None):
+    lib = _load()
+    a = _u8(a)
+    b = _u8(b)
+    n, m = a.size, b.size
+    H = np.empty((n + 1, m + 1), dtype=np.int32)
+    rc = lib.oracle_lcs_table(_ptr(a), n, _ptr(b), m, _ptr(_i32(top)), _ptr(_i32(left)), _ptr(H))
+    if rc != 0:
+        raise ValueError(f"oracle_lcs_table failed ({rc})")
+    return H
+
+
+def lcs_batch(a_cat, a_off, b_cat, b_off, threads=None, boundaries=True):
+    """Per-pair (L[npairs], rows_cat, row_off, cols_cat, col_off); pairs are
+    spread over `threads` host threads (default: all cores)."""
+    lib = _load()
+    a_cat = _u8(a_cat)
+    b_cat = _u8(b_cat)
+    a_off = np.ascontiguousarray(a_off, dtype=np.int64)
+    b_off = np.ascontiguousarray(b_off, dtype=np.int64)
+    npairs = a_off.size - 1
+    n = np.diff(a_off)
+    m = np.diff(b_off)
+    row_off = np.zeros(npairs + 1, dtype=np.int64)
+    row_off[1:] = np.cumsum(m + 1)
+    col_off = np.zeros(npairs + 1, dtype=np.int64)
+    col_off[1:] = np.cumsum(n + 1)
+    L = np.zeros(npairs, dtype=np.int32)
+    rows = np.empty(int(row_off[-1]), dtype=np.int32) if boundaries else None
+    cols = np.empty(int(col_off[-1]), dtype=np.int32) if boundaries else None
+    if threads is None:
+        threads = os.cpu_count() or 1
+    rc = lib.oracle_lcs_batch(_ptr(a_cat), _ptr(a_off), _ptr(b_cat), _ptr(b_off), npairs,
+                              _ptr(L), _ptr(rows), _ptr(row_off), _ptr(cols), _ptr(col_off),
+                              int(threads))
+    if rc != 0:
+        raise ValueError(f"oracle_lcs_batch failed ({rc})")
+    return L, rows, row_off, cols, col_off
