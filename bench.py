@@ -1,0 +1,287 @@
+"""LCS GCUPS benchmark on GB300 (one JSON line on rank 0).
+
+Default workload: one 131072 x 131072 pair (alphabet 20, b = a with exactly
+10% substitutions and 5% single-symbol indels), LCS length plus the last row
+and column, through paco_lcs_boundaries.  A step is one whole pass of the
+path over that pair: boundary preparation, the strip-pipeline kernel, and the
+two boundary prefixes.  Inputs are resident in HBM before timing; the 256 KB
+of inputs fit in L2, so L2 is flushed (a 512 MiB write) between timed steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--config mutated|small|skinny|batch]
+  python bench.py --impl reference ...   # the CPU oracle on a bounded sample
+
+Under torchrun each rank computes its own copy of the workload (independent
+problems: weak scaling, no collective on the data path); the timed region is
+bracketed by a barrier and synchronize and the max over ranks is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2011_01441_gb300 import workloads as W  # noqa: E402
+
+METRIC = "LCS GCUPS on 1 GB300, % of INT32 roofline; served p50/p99 latency vs plain"
+# lane-ops per 32-row column step of the bit-parallel tile (or, and, and-not, add-with-carry)
+OPS_PER_WORD_STEP = 4
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _workload(name):
+    if name == "small":
+        return W.single_small(), "pair 4096x4096 sigma=4 iid (seed 1)"
+    if name == "mutated":
+        return W.single_mutated(), "pair 131072x131072 sigma=20, b = a with 10% subs + 5% indels (seed 2)"
+    if name == "skinny":
+        return W.single_skinny(), "pair 1048576x16384 bytes uniform 0..255 (seed 3)"
+    raise ValueError(name)
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled during the timed region."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def cpu_baseline_pair(a, b, budget_s=12.0):
+    """The oracle as it stands, single thread, on the first rows of the same
+    pair (a bounded sample), extrapolated to GCUPS."""
+    import oracle
+    oracle.build()
+    probe = min(a.size, 512)
+    t = time.perf_counter()
+    oracle.lcs(a[:probe], b)
+    dt = max(time.perf_counter() - t, 1e-6)
+    rows = int(min(a.size, max(probe, probe * budget_s / dt)))
+    t = time.perf_counter()
+    oracle.lcs(a[:rows], b)
+    dt = time.perf_counter() - t
+    return {"value": rows * b.size / dt / 1e9, "unit": "GCUPS", "cores": 1, "kind": "oracle",
+            "sample": f"first {rows} rows x all {b.size} columns of the same pair ({rows * b.size:.3e} cells, {dt:.1f} s)"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    pair, desc = _workload(args.config)
+    for _ in range(args.warmup):
+        cpu_baseline_pair(pair.a, pair.b, budget_s=1.0)
+    vals = []
+    t0 = time.perf_counter()
+    last = None
+    for _ in range(args.steps):
+        last = cpu_baseline_pair(pair.a, pair.b, budget_s=max(2.0, 40.0 / max(1, args.steps)))
+        vals.append(last["value"])
+    el = time.perf_counter() - t0
+    v = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GCUPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic", "config": {"workload": desc, "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": v, "unit": "GCUPS", "cores": 1, "kind": "oracle",
+                             "sample": last["sample"]},
+            "e2e": {"value": v, "unit": "GCUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args):
+    import torch
+    import paper_2011_01441_gb300 as P
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    P.load()
+    ctx = P.Context(local)
+    pair, desc = _workload(args.config)
+    n, m = pair.a.size, pair.b.size
+    da = torch.from_numpy(pair.a).to(dev)
+    db = torch.from_numpy(pair.b).to(dev)
+    row = torch.empty(m + 1, dtype=torch.int32, device=dev)
+    col = torch.empty(n + 1, dtype=torch.int32, device=dev)
+    L = torch.empty(1, dtype=torch.int32, device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        P.paco_lcs_boundaries(ctx, da, db, bottom_row=row, right_col=col, length=L, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    ctx.sync()
+    kernel_ms = []
+    step_ms = []
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        for _ in range(args.steps):
+            flush.fill_(1)  # evict the inputs from L2 between timed steps
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            kernel_ms.append(P.paco_last_kernel_ms(ctx)[0])
+        torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    ctx.sync()
+    tot_ms = sum(step_ms)
+    if ws > 1:
+        t = torch.tensor([tot_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    cells = float(n) * m
+    value = cells * ws * args.steps / (tot_ms * 1e-3) / 1e9
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    ha = torch.from_numpy(pair.a).pin_memory()
+    hb = torch.from_numpy(pair.b).pin_memory()
+    hrow = torch.empty(m + 1, dtype=torch.int32).pin_memory()
+    hcol = torch.empty(n + 1, dtype=torch.int32).pin_memory()
+    hlen = torch.empty(1, dtype=torch.int32)
+    import ctypes
+    vp = lambda t: ctypes.c_void_p(t.data_ptr())
+    P.paco_lcs_boundaries_host_ptr(ctx, vp(ha), n, vp(hb), m, vp(hrow), vp(hcol), vp(hlen))
+    e2e_t = []
+    for _ in range(max(3, args.steps)):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        P.paco_lcs_boundaries_host_ptr(ctx, vp(ha), n, vp(hb), m, vp(hrow), vp(hcol), vp(hlen))
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_val = cells / statistics.median(e2e_t) / 1e9
+    assert int(hlen.item()) == int(L.item())
+
+    # roofline of the dominant kernel: measured integer-ALU issue rate
+    peak_ops = P.paco_measure_int_peak(ctx, 3)
+    kmed = statistics.median(kernel_ms)
+    plan = P.paco_plan_pair(n, m, torch.cuda.get_device_properties(dev).multi_processor_count)
+    word_steps = (plan["L"] + 31) // 32 * plan["S"]
+    achieved = word_steps * OPS_PER_WORD_STEP / (kmed * 1e-3)
+    peaks = _peaks()
+    clk = clocks.summary()
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": "GCUPS", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": desc, "n": n, "m": m, "engine": "bit-parallel strip pipeline",
+                   "chunk": plan["chunk"], "warps_per_cta": plan["warps"], "strips": plan["nstrips"],
+                   "l2": "flushed between timed steps (512 MiB write)"},
+        "kernel_ms_median": kmed,
+        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
+                     "unit": "Tops/s (int32 lane-ops)", "frac": achieved / peak_ops, "traffic": None,
+                     "kernel": "k_pair_bp", "ops_per_cell": OPS_PER_WORD_STEP / 32,
+                     "peak_source": "measured: paco_measure_int_peak(op=3), the kernel's column-step mix on all SMs"},
+        "e2e": {"value": e2e_val, "unit": "GCUPS", "h2d_bytes_per_step": n + m,
+                "d2h_bytes_per_step": 4 * (n + 1) + 4 * (m + 1) + 4},
+        "gpu_launches": 9 * args.steps,
+        "clocks": clk,
+        "hbm_peak_gbs_measured": peaks.get("hbm_gbs"),
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_pair(pair.a, pair.b)
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="mutated", choices=["mutated", "small", "skinny"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

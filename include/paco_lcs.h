@@ -1,0 +1,199 @@
+/*
+ * paco_lcs.h - C ABI of the GB300 LCS wavefront library.
+ *
+ * The library fills the longest-common-subsequence table of Eq. (1) in
+ * Tang & Gao, "Balanced Partitioning of Several Cache-Oblivious Algorithms"
+ * (Sec. "PACO LCS"):
+ *
+ *   H[i][0] = left[i], H[0][j] = top[j]   (zeros when not given, as in Eq. (1))
+ *   H[i][j] = H[i-1][j-1] + 1               if a[i-1] == b[j-1]
+ *           = max(H[i-1][j], H[i][j-1])     otherwise
+ *
+ * for byte strings a (n rows) and b (m columns), and returns the LCS length
+ * L = H[n][m] together with the table's last row bottom_row[j] = H[n][j]
+ * (j = 0..m) and last column right_col[i] = H[i][m] (i = 0..n).  Those two
+ * boundaries are exactly what the paper's execution phase hands from one
+ * region to its neighbours (Sec. "PACO LCS": each sub-region depends only on
+ * its neighbouring regions), so a caller can chain calls over a larger table.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Symbols are raw bytes compared by equality; 0 is an ordinary symbol.
+ * - Lengths n, m are in [0, 2^31 - 1]; anything else returns PACO_EINVAL.
+ * - Device pointers are CUDA global-memory pointers on the context's device.
+ *   `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *   stream).  Device entry points are stream ordered: they return after
+ *   enqueueing; results are valid once the stream reaches that point.
+ * - The caller owns every input and output buffer.  Inputs are never
+ *   written.  The context owns all scratch memory (flags, boundary bit
+ *   buffers, plans) and grows it on demand; scratch is reused across calls,
+ *   so calls on one context must be serialised on one stream (or synchronised
+ *   by the caller).
+ * - Return values: PACO_OK (0), PACO_PENDING (1, poll only) or a negative
+ *   paco_status.  A device-side failure (a bounded wait that timed out)
+ *   cannot be seen at enqueue time: it is recorded in a device error word and
+ *   returned by the next paco_ctx_sync (sticky until then).
+ * - Input boundaries `top`/`left` must be valid LCS boundaries: top[0] ==
+ *   left[0], and each is non-decreasing with steps in {0, 1}.  Every row and
+ *   column of a true LCS table has this property (it is what one region
+ *   receives from its neighbours).  Device-side inputs are checked on the
+ *   device; a violation is reported as PACO_EINVAL by paco_ctx_sync.
+ */
+#ifndef PACO_LCS_H
+#define PACO_LCS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct paco_ctx paco_ctx;
+
+typedef enum paco_status {
+    PACO_OK = 0,
+    PACO_PENDING = 1,     /* paco_lcs_poll: request not finished yet        */
+    PACO_EINVAL = -1,     /* bad argument or invalid boundary               */
+    PACO_ENOMEM = -2,     /* device or host allocation failed               */
+    PACO_ETIMEOUT = -3,   /* a device wait exceeded its limit               */
+    PACO_EDEVICE = -4,    /* a CUDA call failed (message: paco_last_error)  */
+    PACO_EBUSY = -5,      /* serving queue full / budget exhausted          */
+    PACO_ENOTFOUND = -6   /* unknown serving ticket                         */
+} paco_status;
+
+/* ---- context --------------------------------------------------------- */
+
+/* Create a context on CUDA device `device`.  `mem_budget_bytes` bounds the
+ * device memory the serving path may hold for admitted requests (0 = 8 GiB).
+ * Writes the new context to *out.  Errors: PACO_EINVAL (out == NULL or bad
+ * device), PACO_EDEVICE, PACO_ENOMEM. */
+int paco_ctx_create(int device, size_t mem_budget_bytes, paco_ctx **out);
+
+/* Destroy a context: drains its streams and the serving loop, frees its
+ * scratch.  NULL is ignored. */
+void paco_ctx_destroy(paco_ctx *ctx);
+
+/* Human-readable name of a status code (static string). */
+const char *paco_strerror(int status);
+
+/* Last CUDA/diagnostic message recorded on the context (static per ctx). */
+const char *paco_last_error(paco_ctx *ctx);
+
+/* Wait for all work the context enqueued on `stream` (NULL: all of the
+ * context's streams and the caller's last stream) and return the first
+ * sticky device error (PACO_ETIMEOUT, PACO_EINVAL), clearing it. */
+int paco_ctx_sync(paco_ctx *ctx, void *stream);
+
+/* Tunables (engine choice, chunk width, warps per CTA, wait limit ...).
+ * See PACO_OPT_* below.  Returns PACO_EINVAL for an unknown option or a
+ * value out of range. */
+int paco_ctx_set_option(paco_ctx *ctx, int option, int64_t value);
+int paco_ctx_get_option(paco_ctx *ctx, int option, int64_t *value);
+
+enum paco_option {
+    PACO_OPT_ENGINE = 1,        /* 0 = auto, 1 = bit-parallel, 2 = cell-wise   */
+    PACO_OPT_CHUNK = 2,         /* columns per lane hand-off (0 = planner)     */
+    PACO_OPT_WARPS = 3,         /* warps per CTA strip (0 = planner)           */
+    PACO_OPT_WAIT_LIMIT_NS = 4, /* bounded-wait limit per wait, ns (default 2e9) */
+    PACO_OPT_ORIENT = 5,        /* 0 = planner, 1 = bits along a, 2 = along b  */
+    PACO_OPT_SCHEDULE = 6,      /* 0 = PACO balanced strips, 1 = uniform strips */
+    PACO_OPT_TEST_STALL = 100   /* tests only: make one strip wait on a flag
+                                   nothing sets (exercises the bounded wait) */
+};
+
+/* ---- single pair ------------------------------------------------------ */
+
+/* LCS length only.  a: device uint8[n]; b: device uint8[m]; d_len: device
+ * int32[1] receiving L.  Errors: PACO_EINVAL (NULL pointer with a non-zero
+ * length, negative or too-large length), PACO_ENOMEM, PACO_EDEVICE. */
+int paco_lcs_length(paco_ctx *ctx, const uint8_t *a, int64_t n,
+                    const uint8_t *b, int64_t m, int32_t *d_len, void *stream);
+
+/* Length plus boundaries.  d_top_in: device int32[m+1] or NULL (zeros);
+ * d_left_in: device int32[n+1] or NULL (zeros); d_bottom_row: device
+ * int32[m+1] or NULL; d_right_col: device int32[n+1] or NULL; d_len: device
+ * int32[1] or NULL.  Output buffers must not overlap inputs. */
+int paco_lcs_boundaries(paco_ctx *ctx, const uint8_t *a, int64_t n,
+                        const uint8_t *b, int64_t m,
+                        const int32_t *d_top_in, const int32_t *d_left_in,
+                        int32_t *d_bottom_row, int32_t *d_right_col,
+                        int32_t *d_len, void *stream);
+
+/* The same computation from HOST buffers (pageable or pinned): copies a, b
+ * (and the optional host boundaries) to the device, runs, copies the
+ * requested outputs back, and returns when they are in host memory.  Any
+ * output pointer may be NULL. */
+int paco_lcs_boundaries_host(paco_ctx *ctx, const uint8_t *a, int64_t n,
+                             const uint8_t *b, int64_t m,
+                             const int32_t *top_in, const int32_t *left_in,
+                             int32_t *bottom_row, int32_t *right_col,
+                             int32_t *len, void *stream);
+
+/* ---- batch of independent pairs ---------------------------------------- */
+
+/* npairs independent pairs in one persistent launch (captured once into a
+ * CUDA graph per context and size-class layout, then replayed).
+ *   a_cat, b_cat : device uint8, all strings concatenated
+ *   a_off, b_off : device int64[npairs+1], string k is [off[k], off[k+1])
+ *   d_len        : device int32[npairs]
+ *   d_rows_cat   : device int32, row k at row_off[k] with m_k+1 entries (or NULL)
+ *   row_off      : device int64[npairs] (ignored when d_rows_cat is NULL)
+ *   d_cols_cat   : device int32, column k at col_off[k] with n_k+1 entries (or NULL)
+ *   col_off      : device int64[npairs]
+ * The host also needs the pair lengths to plan: h_a_off / h_b_off are the
+ * same offsets in HOST memory (int64[npairs+1]).  Errors: PACO_EINVAL,
+ * PACO_ENOMEM, PACO_EDEVICE. */
+int paco_lcs_batch(paco_ctx *ctx, const uint8_t *a_cat, const int64_t *a_off,
+                   const uint8_t *b_cat, const int64_t *b_off,
+                   const int64_t *h_a_off, const int64_t *h_b_off, int32_t npairs,
+                   int32_t *d_len, int32_t *d_rows_cat, const int64_t *row_off,
+                   int32_t *d_cols_cat, const int64_t *col_off, void *stream);
+
+/* ---- serving: continuous batching ------------------------------------- */
+
+/* Submit one request from HOST memory.  The library copies the strings
+ * before returning (the caller may free them).  The request is admitted to
+ * the device when the context's memory budget allows, runs in a micro-batch
+ * with whatever else is admitted, and is retrieved with paco_lcs_poll.
+ * want_boundaries != 0 keeps bottom_row/right_col for poll.  Writes a ticket.
+ * Errors: PACO_EINVAL, PACO_EBUSY (a single request larger than the budget,
+ * or the host queue is full), PACO_ENOMEM. */
+int paco_lcs_submit(paco_ctx *ctx, const uint8_t *a, int64_t n,
+                    const uint8_t *b, int64_t m, int want_boundaries,
+                    uint64_t *ticket);
+
+/* Poll a ticket.  PACO_PENDING while queued or running; PACO_OK when done,
+ * after writing *len and (if the request kept them and the pointers are not
+ * NULL) HOST row_out[m+1] / col_out[n+1]; the ticket is then released.
+ * PACO_ENOTFOUND for an unknown or already released ticket; a device error
+ * of the request's micro-batch is returned once (and the ticket released). */
+int paco_lcs_poll(paco_ctx *ctx, uint64_t ticket, int32_t *len,
+                  int32_t *row_out, int32_t *col_out);
+
+/* Serving statistics since the context was created (host monotonic clock,
+ * seconds): completed requests, cells, queue and in-flight counts. */
+typedef struct paco_serve_stats {
+    uint64_t submitted, completed, cells_done;
+    uint64_t queued_now, inflight_now, batches_launched;
+    uint64_t bytes_in_use, bytes_budget;
+} paco_serve_stats;
+int paco_serve_get_stats(paco_ctx *ctx, paco_serve_stats *out);
+
+/* ---- measurement helpers ---------------------------------------------- */
+
+/* Device microbenchmark of the 32-bit integer ALU issue rate used as the
+ * roofline denominator: runs independent chains of `op` (0 = IADD3-class
+ * add, 1 = LOP3-class logic, 2 = integer max, 3 = the bit-parallel column
+ * step mix) on every SM and writes lane-operations per second to *out. */
+int paco_measure_int_peak(paco_ctx *ctx, int op, double *ops_per_s, void *stream);
+
+/* Kernel time (ms, CUDA events on the launching stream) of the dominant
+ * kernel of the last paco_lcs_* call on this context, and its name. */
+int paco_last_kernel_ms(paco_ctx *ctx, double *ms, const char **name);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PACO_LCS_H */

@@ -1,0 +1,65 @@
+/*
+ * paco_plan.h - host-only planner introspection (no GPU needed).
+ *
+ * The partition follows the PACO LCS partitioning phase of Tang & Gao,
+ * Sec. "PACO LCS" (and its proof's simplification that the first step is a
+ * p-way division): the table is cut p ways in each dimension, then regions
+ * are repeatedly halved in both dimensions; whenever an anti-diagonal holds
+ * at least p unassigned regions, p of them are assigned round-robin to the
+ * p processors; regions that can no longer be halved (a side below 2*base)
+ * are assigned round-robin.  Regions are returned in time-line order: each
+ * after every region it depends on (its neighbours above and to the left).
+ *
+ * The pair plan is what the bit-parallel strip pipeline executes for one
+ * table: the p-way balanced split of the rows into CTA strips.
+ */
+#ifndef PACO_PLAN_H
+#define PACO_PLAN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct paco_tile {
+    int64_t r0, r1, c0, c1; /* DP cells: rows [r0, r1), columns [c0, c1), 0-based */
+    int32_t label;          /* assignment round (1 = the first p-way regions)      */
+    int32_t owner;          /* processor 0..p-1                                      */
+    int64_t order;          /* position in the time line                             */
+} paco_tile;
+
+/* Partition an n x m table for p processors, stopping at regions whose
+ * sides cannot be halved without dropping below `base`.  Writes up to `cap`
+ * tiles to `out` (may be NULL to query the count) and the total to *count.
+ * Returns 0, or -1 (PACO_EINVAL) for n, m, p, base <= 0. */
+int paco_plan_partition(int64_t n, int64_t m, int32_t p, int64_t base, paco_tile *out, int64_t cap,
+                        int64_t *count);
+
+/* Dependencies of every tile of the partition above, as a CSR list over
+ * the returned order: dep_off[k]..dep_off[k+1] index dep_idx.  dep_off has
+ * count+1 entries; dep_idx capacity `cap_idx`.  Returns 0 or -1. */
+int paco_plan_partition_deps(int64_t n, int64_t m, int32_t p, int64_t base, int64_t *dep_off,
+                             int64_t *dep_idx, int64_t cap_idx, int64_t *n_idx);
+
+typedef struct paco_pair_plan {
+    int32_t transpose;  /* 1: bits run along b                                 */
+    int32_t chunk;      /* columns per lane hand-off                          */
+    int32_t warps;      /* warps per CTA strip                                */
+    int32_t nstrips;    /* CTA strips (the p of the balanced row split)       */
+    int64_t L, S;       /* kernel rows (bit dimension) and streamed columns   */
+} paco_pair_plan;
+
+/* Plan one pair for a device with `sms` multiprocessors.  chunk/warps 0 =
+ * planner's choice; orient 0 = bits along the longer string, 1 = along a,
+ * 2 = along b; schedule 0 = balanced strips, 1 = uniform strips.
+ * row0 (capacity cap, may be NULL) receives nstrips+1 strip row offsets.
+ * Returns 0 or -1. */
+int paco_plan_pair(int64_t n, int64_t m, int32_t sms, int32_t chunk, int32_t warps, int32_t orient,
+                   int32_t schedule, paco_pair_plan *out, int64_t *row0, int64_t cap);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PACO_PLAN_H */

@@ -1,0 +1,70 @@
+// The context object behind the opaque paco_ctx handle.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <memory>
+#include <mutex>
+#include <tuple>
+
+#include "plan.hpp"
+
+struct DevBuf {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+};
+
+namespace paco {
+struct BatchState;
+struct ServeEngine;
+
+// A pair plan plus its strip offsets resident on the device.
+struct CachedPairPlan {
+    PairPlan plan;
+    DevBuf d_row0;
+};
+}  // namespace paco
+
+struct paco_ctx {
+    int device = 0;
+    int sms = 0;
+    size_t budget = 0;
+    std::mutex mu;
+    // small: [0] error word, [1] ticket, sink from byte 1024
+    DevBuf small;
+    // single-pair scratch
+    DevBuf hbuf, lbits, rbits, rows, sums;
+    // staging for the host-buffer entry point
+    DevBuf h_a, h_b, h_top, h_left, h_row, h_col, h_len;
+    uint32_t epoch = 0;
+    int opt_engine = 0, opt_chunk = 0, opt_warps = 0, opt_orient = 0, opt_schedule = 0;
+    int test_stall = -1;
+    long long wait_limit_ns = 2000000000LL;
+    char last_error[256] = {0};
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    bool timed = false;
+    const char *timed_name = "";
+    cudaStream_t own_stream = nullptr;
+    std::map<std::tuple<int64_t, int64_t, int, int, int, int>, std::unique_ptr<paco::CachedPairPlan>> plans;
+    paco::BatchState *batch = nullptr;
+    paco::ServeEngine *serve = nullptr;
+
+    int *err_ptr() { return (int *)small.ptr; }
+    int *ticket_ptr() { return (int *)small.ptr + 1; }
+    uint32_t *sink_ptr() { return (uint32_t *)((char *)small.ptr + 1024); }
+};
+
+namespace paco {
+int set_cuda_error(paco_ctx *ctx, cudaError_t e, const char *where);
+int ensure_bytes(paco_ctx *ctx, DevBuf &buf, size_t bytes);
+uint32_t next_epoch(paco_ctx *ctx);
+// Enqueue one pair (device pointers) on `st`; ctx->mu must be held.
+int run_pair(paco_ctx *ctx, const uint8_t *a, int64_t n, const uint8_t *b, int64_t m,
+             const int32_t *top, const int32_t *left, int32_t *bottom_row, int32_t *right_col,
+             int32_t *len, cudaStream_t st);
+const CachedPairPlan *get_pair_plan(paco_ctx *ctx, int64_t n, int64_t m, int *rc);
+void serve_shutdown(paco_ctx *ctx);
+void batch_release(paco_ctx *ctx);
+}  // namespace paco

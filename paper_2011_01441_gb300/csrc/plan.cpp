@@ -1,0 +1,226 @@
+// Host-side planner (see plan.hpp).
+#include "plan.hpp"
+
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <queue>
+#include <tuple>
+
+namespace paco {
+
+std::vector<int64_t> balanced_split(int64_t total, int64_t parts) {
+    std::vector<int64_t> sizes;
+    if (parts <= 0) return sizes;
+    sizes.resize((size_t)parts, total / parts);
+    for (int64_t k = 0; k < total % parts; ++k) sizes[(size_t)k] += 1;
+    return sizes;
+}
+
+namespace {
+
+struct Reg {
+    int64_t r0, r1, c0, c1;
+    int64_t gi, gj;  // grid index at the region's level
+};
+
+bool divisible(const Reg &r, int64_t base) {
+    return (r.r1 - r.r0) >= 2 * base && (r.c1 - r.c0) >= 2 * base;
+}
+
+}  // namespace
+
+bool paco_partition(int64_t n, int64_t m, int32_t p, int64_t base, std::vector<Tile> &tiles) {
+    tiles.clear();
+    if (n <= 0 || m <= 0 || p <= 0 || base <= 0) return false;
+    // Step 1: the p-way division in both dimensions (balanced integer split).
+    const int64_t pr = std::min<int64_t>(p, n), pc = std::min<int64_t>(p, m);
+    const std::vector<int64_t> hs = balanced_split(n, pr), ws = balanced_split(m, pc);
+    std::vector<Reg> un;
+    un.reserve((size_t)(pr * pc));
+    int64_t r = 0;
+    for (int64_t i = 0; i < pr; ++i) {
+        int64_t c = 0;
+        for (int64_t j = 0; j < pc; ++j) {
+            un.push_back({r, r + hs[(size_t)i], c, c + ws[(size_t)j], i, j});
+            c += ws[(size_t)j];
+        }
+        r += hs[(size_t)i];
+    }
+    int32_t label = 1;
+    int64_t rr = 0;  // round-robin counter of base-case assignments
+    while (!un.empty()) {
+        // group by anti-diagonal of the level grid; within one, ascending column
+        std::map<int64_t, std::vector<Reg>> diag;
+        for (const Reg &x : un) diag[x.gi + x.gj].push_back(x);
+        std::vector<Reg> left;
+        bool assigned_any = false;
+        for (auto &kv : diag) {
+            std::vector<Reg> &v = kv.second;
+            std::sort(v.begin(), v.end(), [](const Reg &a, const Reg &b) { return a.gj < b.gj; });
+            size_t take = v.size() >= (size_t)p ? (size_t)p : 0;
+            for (size_t k = 0; k < take; ++k)
+                tiles.push_back({v[k].r0, v[k].r1, v[k].c0, v[k].c1, label, (int32_t)k, 0});
+            if (take) assigned_any = true;
+            for (size_t k = take; k < v.size(); ++k) left.push_back(v[k]);
+        }
+        // base-case regions (cannot be halved): all of them round-robin
+        std::vector<Reg> next;
+        bool base_assigned = false;
+        std::sort(left.begin(), left.end(), [](const Reg &a, const Reg &b) {
+            return std::make_tuple(a.gi + a.gj, a.gj) < std::make_tuple(b.gi + b.gj, b.gj);
+        });
+        for (const Reg &x : left) {
+            if (!divisible(x, base)) {
+                tiles.push_back({x.r0, x.r1, x.c0, x.c1, label, (int32_t)(rr % p), 0});
+                ++rr;
+                base_assigned = true;
+            } else {
+                const int64_t hm = x.r0 + (x.r1 - x.r0) / 2, wm = x.c0 + (x.c1 - x.c0) / 2;
+                next.push_back({x.r0, hm, x.c0, wm, 2 * x.gi, 2 * x.gj});
+                next.push_back({x.r0, hm, wm, x.c1, 2 * x.gi, 2 * x.gj + 1});
+                next.push_back({hm, x.r1, x.c0, wm, 2 * x.gi + 1, 2 * x.gj});
+                next.push_back({hm, x.r1, wm, x.c1, 2 * x.gi + 1, 2 * x.gj + 1});
+            }
+        }
+        if (assigned_any || base_assigned) ++label;
+        un.swap(next);
+    }
+    // time line: Kahn's algorithm over the region DAG, earliest anti-diagonal first
+    std::vector<std::vector<int64_t>> deps;
+    tile_deps(tiles, deps);
+    const size_t T = tiles.size();
+    std::vector<std::vector<int64_t>> succ(T);
+    std::vector<int64_t> indeg(T, 0);
+    for (size_t k = 0; k < T; ++k) {
+        indeg[k] = (int64_t)deps[k].size();
+        for (int64_t d : deps[k]) succ[(size_t)d].push_back((int64_t)k);
+    }
+    using Key = std::tuple<int64_t, int64_t, int64_t>;  // (2*center anti-diagonal, r0, index)
+    std::priority_queue<Key, std::vector<Key>, std::greater<Key>> ready;
+    auto key = [&](size_t k) {
+        const Tile &t = tiles[k];
+        return Key{t.r0 + t.r1 + t.c0 + t.c1, t.r0, (int64_t)k};
+    };
+    for (size_t k = 0; k < T; ++k)
+        if (indeg[k] == 0) ready.push(key(k));
+    int64_t pos = 0;
+    std::vector<Tile> ordered;
+    ordered.reserve(T);
+    while (!ready.empty()) {
+        const size_t k = (size_t)std::get<2>(ready.top());
+        ready.pop();
+        tiles[k].order = pos++;
+        ordered.push_back(tiles[k]);
+        for (int64_t s : succ[k])
+            if (--indeg[(size_t)s] == 0) ready.push(key((size_t)s));
+    }
+    if (ordered.size() != T) return false;  // a cycle cannot happen for a partition
+    tiles.swap(ordered);
+    return true;
+}
+
+void tile_deps(const std::vector<Tile> &tiles, std::vector<std::vector<int64_t>> &deps) {
+    const size_t T = tiles.size();
+    deps.assign(T, {});
+    // index tiles by bottom edge (sorted by c0) and by right edge (sorted by r0)
+    std::map<int64_t, std::vector<int64_t>> by_r1, by_c1;
+    for (size_t k = 0; k < T; ++k) {
+        by_r1[tiles[k].r1].push_back((int64_t)k);
+        by_c1[tiles[k].c1].push_back((int64_t)k);
+    }
+    for (auto &kv : by_r1)
+        std::sort(kv.second.begin(), kv.second.end(),
+                  [&](int64_t a, int64_t b) { return tiles[(size_t)a].c0 < tiles[(size_t)b].c0; });
+    for (auto &kv : by_c1)
+        std::sort(kv.second.begin(), kv.second.end(),
+                  [&](int64_t a, int64_t b) { return tiles[(size_t)a].r0 < tiles[(size_t)b].r0; });
+    for (size_t k = 0; k < T; ++k) {
+        const Tile &t = tiles[k];
+        std::vector<int64_t> &d = deps[k];
+        if (t.r0 > 0) {  // tiles above, columns [c0-1, c1)
+            auto it = by_r1.find(t.r0);
+            if (it != by_r1.end()) {
+                const int64_t lo = std::max<int64_t>(0, t.c0 - 1), hi = t.c1;
+                for (int64_t x : it->second) {
+                    const Tile &u = tiles[(size_t)x];
+                    if (u.c0 >= hi) break;
+                    if (u.c1 > lo) d.push_back(x);
+                }
+            }
+        }
+        if (t.c0 > 0) {  // tiles to the left, rows [r0-1, r1)
+            auto it = by_c1.find(t.c0);
+            if (it != by_c1.end()) {
+                const int64_t lo = std::max<int64_t>(0, t.r0 - 1), hi = t.r1;
+                for (int64_t x : it->second) {
+                    const Tile &u = tiles[(size_t)x];
+                    if (u.r0 >= hi) break;
+                    if (u.r1 > lo) d.push_back(x);
+                }
+            }
+        }
+        std::sort(d.begin(), d.end());
+        d.erase(std::unique(d.begin(), d.end()), d.end());
+    }
+}
+
+bool plan_pair(int64_t n, int64_t m, int sms, const PairPlanOptions &o, PairPlan &out) {
+    if (n <= 0 || m <= 0 || sms <= 0) return false;
+    out = PairPlan();
+    out.transpose = o.orient == 2 || (o.orient == 0 && m > n);
+    out.L = out.transpose ? m : n;
+    out.S = out.transpose ? n : m;
+    // chunk width: minimise (S/C + L/32) * (C*c_col + c_hop), the critical path of the
+    // lane pipeline (c_col ~ cycles of one dependent column step, c_hop ~ a shuffle hop)
+    if (o.chunk) {
+        out.C = o.chunk;
+    } else {
+        const double c_col = 9.0, c_hop = 25.0;
+        double best = 1e300;
+        for (int C = 1; C <= 32; C *= 2) {
+            const double cost = ((double)out.S / C + (double)out.L / 32.0) * (C * c_col + c_hop);
+            if (cost < best) {
+                best = cost;
+                out.C = C;
+            }
+        }
+    }
+    const int64_t warps_total = (out.L + 1023) / 1024;
+    int W = o.warps > 0 ? o.warps : 4;
+    W = std::max(1, std::min(W, o.max_warps));
+    if ((int64_t)W > warps_total) W = (int)warps_total;
+    int64_t nstrips = (warps_total + W - 1) / W;
+    if (o.warps == 0 && o.resident > 0 && nstrips > o.resident) {
+        // keep every strip resident when shared memory allows taller CTA strips
+        const int64_t need = (warps_total + o.resident - 1) / o.resident;
+        if (need <= o.max_warps) {
+            W = (int)need;
+            nstrips = (warps_total + W - 1) / W;
+        }
+    }
+    out.W = W;
+    if (o.schedule == 1) {
+        const int64_t h = (int64_t)W * 1024;
+        nstrips = (out.L + h - 1) / h;
+        out.row0.resize((size_t)nstrips + 1);
+        for (int64_t k = 0; k <= nstrips; ++k) out.row0[(size_t)k] = std::min(out.L, k * h);
+    } else {
+        // the p-way first division of the PACO partition on rows, p = nstrips,
+        // in 32-row granules (parts differ by at most one granule)
+        const int64_t G = (out.L + 31) / 32;
+        const std::vector<int64_t> parts = balanced_split(G, nstrips);
+        out.row0.resize((size_t)nstrips + 1);
+        int64_t acc = 0;
+        out.row0[0] = 0;
+        for (int64_t k = 0; k < nstrips; ++k) {
+            acc += parts[(size_t)k];
+            out.row0[(size_t)k + 1] = std::min(out.L, acc * 32);
+        }
+    }
+    out.nstrips = (int)nstrips;
+    out.grid = o.resident > 0 ? (int)std::min<int64_t>(nstrips, o.resident) : (int)nstrips;
+    return true;
+}
+
+}  // namespace paco

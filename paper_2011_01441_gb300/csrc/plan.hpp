@@ -1,0 +1,65 @@
+// Host-side planner: the PACO partition of the LCS table (Sec. "PACO LCS")
+// and the strip plan the bit-parallel pipeline executes.  Pure C++ (no CUDA),
+// so it is testable on a machine without a GPU through include/paco_plan.h.
+#pragma once
+
+#include <stdint.h>
+
+#include <vector>
+
+namespace paco {
+
+// ---- the paper's partition, re-derived for an n x m table and any p ----
+//
+// Step 1 (the proof's simplification, "the first step of partitioning makes
+// a p-way division"): rows and columns are each cut p ways by the balanced
+// integer split (parts differ by at most one row/column).  Then, repeatedly:
+// group the unassigned regions of the current level by anti-diagonal (equal
+// row-index + column-index of the level's grid); every anti-diagonal holding
+// at least p of them gets p regions assigned round-robin to processors
+// 0..p-1 (the p with the smallest column index); when no unassigned region
+// can be halved any more (a side would drop below `base`), all remaining
+// ones are assigned round-robin; otherwise each unassigned region is divided
+// 2-way in both dimensions (a quadtree step) and the next level starts.
+struct Tile {
+    int64_t r0, r1, c0, c1;  // rows [r0, r1), columns [c0, c1) of the DP cells (0-based)
+    int32_t label;           // assignment round, 1 = first (largest regions)
+    int32_t owner;           // processor 0..p-1
+    int64_t order;           // position in the execution time line (topological)
+};
+
+// Returns false on bad arguments.  `tiles` receives the regions in time-line
+// order (each region after every region it depends on).
+bool paco_partition(int64_t n, int64_t m, int32_t p, int64_t base, std::vector<Tile> &tiles);
+
+// Dependencies of tile k: every tile whose bottom edge touches k's top edge,
+// whose right edge touches k's left edge, or that holds the cell diagonally
+// above-left of k's corner.
+void tile_deps(const std::vector<Tile> &tiles, std::vector<std::vector<int64_t>> &deps);
+
+// ---- the strip plan of the bit-parallel pipeline ----
+struct PairPlan {
+    bool transpose = false;  // true: bits along b (rows of the kernel = b)
+    int C = 8;               // columns per lane hand-off
+    int W = 4;               // warps per CTA strip
+    int nstrips = 1;         // CTA strips (the p of the balanced split)
+    int grid = 1;            // CTAs launched (<= nstrips)
+    int64_t L = 0, S = 0;    // kernel rows (bit dimension) and streamed columns
+    std::vector<int64_t> row0;  // nstrips+1 offsets, multiples of 32, row0[nstrips] = L
+};
+
+struct PairPlanOptions {
+    int chunk = 0;      // 0: cost model
+    int warps = 0;      // 0: default
+    int orient = 0;     // 0: bits along the longer string; 1: along a; 2: along b
+    int schedule = 0;   // 0: balanced strips (p-way split); 1: uniform strips of W*1024 rows
+    int max_warps = 7;  // shared-memory limit per CTA
+    int resident = 0;   // CTAs that fit on the device at once (0: unknown)
+};
+
+bool plan_pair(int64_t n, int64_t m, int sms, const PairPlanOptions &o, PairPlan &out);
+
+// Balanced integer split of `total` units into `parts` (first total%parts get one more).
+std::vector<int64_t> balanced_split(int64_t total, int64_t parts);
+
+}  // namespace paco

@@ -1,0 +1,174 @@
+"""CPU-only checks: the C-ABI library loads and exports every declared
+symbol; the planner's partition satisfies the paper's structural claims."""
+import os
+import re
+from collections import Counter, defaultdict
+
+import numpy as np
+import pytest
+
+import paper_2011_01441_gb300 as P
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = []
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not h.endswith(".h"):
+            continue
+        txt = open(os.path.join(ROOT, "include", h)).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s*(paco_[a-z0-9_]+)\s*\(", txt, re.M):
+            names.append(m.group(1))
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__
+    __graft_entry__.build()
+    return P.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared_functions()
+    expected = {"paco_ctx_create", "paco_ctx_destroy", "paco_strerror", "paco_last_error",
+                "paco_ctx_sync", "paco_ctx_set_option", "paco_ctx_get_option", "paco_lcs_length",
+                "paco_lcs_boundaries", "paco_lcs_boundaries_host", "paco_lcs_batch",
+                "paco_lcs_submit", "paco_lcs_poll", "paco_serve_get_stats",
+                "paco_measure_int_peak", "paco_last_kernel_ms", "paco_plan_partition",
+                "paco_plan_partition_deps", "paco_plan_pair"}
+    assert expected <= set(names), expected - set(names)
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_strerror_is_static_text(lib):
+    assert P._strerror(P.PACO_ETIMEOUT) == "device wait timed out"
+    assert P._strerror(P.PACO_EINVAL) == "invalid argument"
+
+
+def _cover(tiles, n, m):
+    grid = np.zeros((n, m), dtype=np.int32)
+    for t in tiles:
+        grid[t["r0"]:t["r1"], t["c0"]:t["c1"]] += 1
+    return grid
+
+
+@pytest.mark.parametrize("n,m,p,base", [(64, 64, 4, 2), (97, 131, 3, 2), (300, 120, 7, 3),
+                                        (1000, 1000, 37, 4), (257, 257, 1, 8), (40, 40, 2, 1)])
+def test_partition_exact_cover_and_topological(lib, n, m, p, base):
+    tiles = P.paco_plan_partition(n, m, p, base)
+    assert np.all(_cover(tiles, n, m) == 1)
+    assert [t["order"] for t in tiles] == list(range(len(tiles)))
+    assert all(0 <= t["owner"] < p for t in tiles)
+    off, idx = P.paco_plan_partition_deps(n, m, p, base)
+    for k in range(len(tiles)):
+        for d in idx[off[k]:off[k + 1]]:
+            assert d < k  # every dependency runs earlier on the time line
+            u, t = tiles[d], tiles[k]
+            touches_top = u["r1"] == t["r0"] and u["c0"] < t["c1"] and u["c1"] >= t["c0"]
+            touches_left = u["c1"] == t["c0"] and u["r0"] < t["r1"] and u["r1"] >= t["r0"]
+            assert touches_top or touches_left
+
+
+def test_partition_dependencies_are_complete(lib):
+    """Brute force: tile k must list every tile containing a cell directly
+    above, directly left or diagonally above-left of one of its cells."""
+    n, m, p, base = 48, 40, 3, 2
+    tiles = P.paco_plan_partition(n, m, p, base)
+    owner = np.full((n, m), -1)
+    for k, t in enumerate(tiles):
+        owner[t["r0"]:t["r1"], t["c0"]:t["c1"]] = k
+    off, idx = P.paco_plan_partition_deps(n, m, p, base)
+    for k, t in enumerate(tiles):
+        need = set()
+        for i in range(t["r0"], t["r1"]):
+            for j in range(t["c0"], t["c1"]):
+                for di, dj in ((-1, 0), (0, -1), (-1, -1)):
+                    ii, jj = i + di, j + dj
+                    if ii >= 0 and jj >= 0 and owner[ii, jj] != k:
+                        need.add(int(owner[ii, jj]))
+        assert need == set(int(x) for x in idx[off[k]:off[k + 1]]), k
+
+
+def test_partition_p4_matches_figure(lib):
+    """Fig. "PACO LCS (p=4)": the label-1 regions are the p regions of the
+    middle anti-diagonal, each of side n/p; label 2 puts p regions on each of
+    p-1 anti-diagonals of every corner triangle (2(p-1) per processor)."""
+    n, p = 256, 4
+    tiles = P.paco_plan_partition(n, n, p, 8)
+    lab = defaultdict(list)
+    for t in tiles:
+        lab[t["label"]].append(t)
+    one = lab[1]
+    assert len(one) == p
+    for k, t in enumerate(sorted(one, key=lambda t: t["c0"])):
+        assert (t["r1"] - t["r0"], t["c1"] - t["c0"]) == (n // p, n // p)
+        assert t["r0"] // (n // p) + t["c0"] // (n // p) == p - 1  # middle anti-diagonal
+    two = lab[2]
+    assert len(two) == 2 * p * (p - 1)
+    assert all((t["r1"] - t["r0"]) == n // (2 * p) for t in two)
+    assert Counter(t["owner"] for t in two) == {o: 2 * (p - 1) for o in range(p)}
+
+
+@pytest.mark.parametrize("p", [2, 3, 4, 5, 7, 37])
+def test_partition_label_doubling_and_balance(lib, p):
+    """From label 2 on, each processor's count of label-(j+1) regions is twice
+    its label-j count while regions are halved, and per-processor cell totals
+    differ by no more than one base-case region per label (the "optimal
+    balanced computation" criterion)."""
+    n, base = 64 * p, 4
+    tiles = P.paco_plan_partition(n, n, p, base)
+    per_label_owner = defaultdict(Counter)
+    sizes = defaultdict(set)
+    for t in tiles:
+        per_label_owner[t["label"]][t["owner"]] += 1
+        sizes[t["label"]].add(t["r1"] - t["r0"])
+    labels = sorted(per_label_owner)
+    for j in labels[1:-2]:
+        if j + 1 in per_label_owner and max(sizes[j + 1]) * 2 <= max(sizes[j]) + 1:
+            for o in range(p):
+                assert per_label_owner[j + 1][o] == 2 * per_label_owner[j][o], (j, o)
+    cells = Counter()
+    for t in tiles:
+        cells[t["owner"]] += (t["r1"] - t["r0"]) * (t["c1"] - t["c0"])
+    biggest_leaf = max((t["r1"] - t["r0"]) * (t["c1"] - t["c0"]) for t in tiles if t["label"] == labels[-1])
+    assert max(cells.values()) - min(cells.values()) <= (len(labels) + 1) * max(biggest_leaf, 4 * base * base)
+
+
+def test_partition_leaf_count_formula(lib):
+    """Corollary on partitioning overheads: while every level is assigned in
+    full groups of p, the leaves number p[1 + sum_i 2^(i-1)(p-1)]."""
+    p = 4
+    n = 16 * p
+    tiles = P.paco_plan_partition(n, n, p, 4)
+    labels = Counter(t["label"] for t in tiles)
+    assert labels[1] == p
+    for i in range(2, 3):
+        assert labels[i] == p * (2 ** (i - 1)) * (p - 1)
+
+
+@pytest.mark.parametrize("n,m,sms", [(131072, 131072, 148), (131072, 131072, 152),
+                                     (1048576, 16384, 152), (16384, 1048576, 152),
+                                     (4096, 4096, 152), (1000, 3, 152), (33, 1, 7)])
+def test_pair_plan_balanced_strips(lib, n, m, sms):
+    pl = P.paco_plan_pair(n, m, sms)
+    L = max(n, m)
+    assert pl["L"] == L and pl["S"] == min(n, m)
+    assert pl["transpose"] == (1 if m > n else 0)
+    row0 = pl["row0"]
+    assert row0[0] == 0 and row0[-1] == L
+    h = np.diff(row0)
+    assert np.all(h > 0) and np.all(row0[:-1] % 32 == 0)
+    assert np.all(h <= pl["warps"] * 1024)
+    if h.size > 2:
+        assert h[:-1].max() - h[:-1].min() <= 32  # the +-1 granule split of the p-way division
+    assert pl["chunk"] in (1, 2, 4, 8, 16, 32)
+
+
+def test_pair_plan_options(lib):
+    pl = P.paco_plan_pair(5000, 7000, 152, chunk=4, warps=2, orient=1, schedule=1)
+    assert pl["transpose"] == 0 and pl["chunk"] == 4 and pl["warps"] == 2
+    assert list(pl["row0"]) == [0, 2048, 4096, 5000]
