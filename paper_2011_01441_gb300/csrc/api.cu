@@ -122,7 +122,7 @@ void paco_ctx_destroy(paco_ctx *ctx) {
     serve_shutdown(ctx);
     cudaDeviceSynchronize();
     batch_release(ctx);
-    for (DevBuf *b : {&ctx->small, &ctx->hbuf, &ctx->lbits, &ctx->rbits, &ctx->rows, &ctx->sums,
+    for (DevBuf *b : {&ctx->small, &ctx->hbuf, &ctx->lbits, &ctx->rbits, &ctx->rows, &ctx->sums, &ctx->boff,
                       &ctx->h_a, &ctx->h_b, &ctx->h_top, &ctx->h_left, &ctx->h_row, &ctx->h_col,
                       &ctx->h_len}) {
         if (b->ptr) cudaFree(b->ptr);
@@ -142,7 +142,7 @@ int paco_ctx_set_option(paco_ctx *ctx, int option, int64_t value) {
             ctx->opt_engine = (int)value;
             return PACO_OK;
         case PACO_OPT_CHUNK:
-            if (!(value == 0 || value == 1 || value == 2 || value == 4 || value == 8 || value == 16 ||
+            if (!(value == 0 || value == 2 || value == 4 || value == 8 || value == 16 ||
                   value == 32))
                 return PACO_EINVAL;
             ctx->opt_chunk = (int)value;

@@ -16,8 +16,9 @@ constexpr int kMaxSigma = 256;
 // Slots of the shared-memory ring that hands carry words from one warp of a
 // CTA strip to the next.
 constexpr int kRing = 32;
-// Rows one warp holds as 32 lanes x 32 bits.
-constexpr int kWarpRows = 1024;
+// Rows one lane holds (bit 31 of its word is the carry slot) and one warp holds.
+constexpr int kLaneRowsH = 31;
+constexpr int kWarpRows = 31 * 32;
 
 // ---------------------------------------------------------------------------
 // Single pair, bit-parallel strip pipeline.
@@ -34,15 +35,17 @@ constexpr int kWarpRows = 1024;
 struct PairArgs {
     const uint8_t *a;            // row string (bits), length L
     const uint8_t *b;            // column string (streamed), length S
+    const uint32_t *boff;        // S byte offsets of the columns' match-table rows
     int64_t L, S;
     int64_t nchunks;             // ceil(S / C)
     int64_t nwords;              // ceil(S / 32): words per carry row
-    const int64_t *strip_row0;   // nstrips+1 row offsets (multiples of 32, last = L)
+    int64_t hstride;             // words between carry rows (nwords rounded up to even)
+    const int64_t *strip_row0;   // nstrips+1 row offsets (multiples of 31, last = L)
     int nstrips;
     int sigma;                   // match-table rows (symbols must be < sigma)
     const uint32_t *left_bits;   // L bits: vertical steps of the first column
-    uint32_t *right_bits;        // L bits out: vertical steps of the last column
-    uint64_t *hbuf;              // (nstrips+1) x nwords tagged carry words; row 0 = input top
+    uint32_t *right_bits;        // ceil(L/31) lane words out: vertical steps of the last column
+    uint64_t *hbuf;              // (nstrips+1) x hstride tagged carry words; row 0 = input top
     int *ticket;                 // strip ticket counter (zeroed before launch)
     int *err;                    // device error word
     uint32_t epoch;              // tag of this launch (never 0)
@@ -62,10 +65,12 @@ cudaError_t launch_boundary_bits(const int32_t *v, int64_t len, uint32_t *bits,
                                  const int32_t *other, int *err, cudaStream_t st);
 // Bits (tagged or plain) -> int32 prefix output with a base value.
 struct PrefixScratch { int64_t *block_sums; int64_t cap; };
-cudaError_t launch_bits_prefix(const uint32_t *bits, const uint64_t *tagged, int64_t nbits,
+// bpw: elements per word (32: packed bit rows; 31: lane words).
+cudaError_t launch_bits_prefix(const uint32_t *bits, const uint64_t *tagged, int64_t nbits, int bpw,
                                const int32_t *base_ptr, int64_t base_index,
                                int32_t *out, int32_t *len_out,
                                PrefixScratch &scr, cudaStream_t st);
+cudaError_t launch_column_offsets(const uint8_t *b, int64_t S, uint32_t *boff, cudaStream_t st);
 // n == 0 or m == 0 tables: copy/zero the boundaries.
 cudaError_t launch_degenerate(const int32_t *top, const int32_t *left, int64_t n, int64_t m,
                               int32_t *bottom_row, int32_t *right_col, int32_t *len,

@@ -50,123 +50,136 @@ __device__ __forceinline__ void raise_error(int *err, int code) { atomicCAS(err,
 
 constexpr size_t kTableBytes = (size_t)kMaxSigma * 32 * sizeof(uint32_t);  // per warp
 
-// Lane 0 polls a global tagged word until its tag is `want`; the result is
-// broadcast to the warp.  Bounded: on timeout or a raised error the warp
-// gets ok == false.
-__device__ __forceinline__ uint64_t poll_global(const uint64_t *p, uint32_t want, const PairArgs &P,
-                                                bool &ok) {
-    const int lane = threadIdx.x & 31;
-    uint64_t v = 0;
-    int good = 1;
-    if (lane == 0) {
+// One lane polls a global tagged word until its tag is `want`.  Bounded: on
+// timeout or a raised error `ok` turns false (the caller ends the strip).
+__device__ __noinline__ uint64_t poll_global_lane(const uint64_t *p, uint32_t want, int *err,
+                                                  long long limit, bool &ok) {
+    uint64_t v = ld_relaxed_u64(p);
+    if ((uint32_t)(v >> 32) == want) return v;
+    const uint64_t t0 = global_ns();
+    for (int spin = 0;; ++spin) {
+        if (spin > 16) __nanosleep(32);
         v = ld_relaxed_u64(p);
-        if ((uint32_t)(v >> 32) != want) {
-            const uint64_t t0 = global_ns();
-            for (;;) {
-                __nanosleep(64);
-                v = ld_relaxed_u64(p);
-                if ((uint32_t)(v >> 32) == want) break;
-                if (ld_relaxed_i32(P.err) != 0) { good = 0; break; }
-                if ((long long)(global_ns() - t0) > P.wait_limit_ns) {
-                    raise_error(P.err, kEtimeout);
-                    good = 0;
-                    break;
-                }
-            }
+        if ((uint32_t)(v >> 32) == want) return v;
+        if (ld_relaxed_i32(err) != 0) {
+            ok = false;
+            return v;
+        }
+        if ((long long)(global_ns() - t0) > limit) {
+            raise_error(err, kEtimeout);
+            ok = false;
+            return v;
         }
     }
-    good = __shfl_sync(kFull, good, 0);
-    ok = good != 0;
-    const uint32_t lo = __shfl_sync(kFull, (uint32_t)v, 0);
-    const uint32_t hi = __shfl_sync(kFull, (uint32_t)(v >> 32), 0);
-    return ((uint64_t)hi << 32) | lo;
 }
 
-// Lane 0 waits for slot (t mod kRing) of a shared ring to carry tag t+1.
-__device__ __forceinline__ uint32_t poll_ring(const uint64_t *ring, int64_t t, const PairArgs &P,
-                                              bool &ok) {
-    const int lane = threadIdx.x & 31;
-    uint64_t v = 0;
-    int good = 1;
-    if (lane == 0) {
-        const volatile uint64_t *slot = ring + (t % kRing);
-        const uint32_t want = (uint32_t)(t + 1);
+// One lane waits for slot (u mod kRing) of a shared ring to carry tag u+1.
+__device__ __noinline__ uint32_t poll_ring_lane(const uint64_t *ring, int64_t u, int *err, long long limit,
+                                                bool &ok) {
+    const volatile uint64_t *slot = ring + (u % kRing);
+    const uint32_t want = (uint32_t)(u + 1);
+    uint64_t v = *slot;
+    if ((uint32_t)(v >> 32) == want) return (uint32_t)v;
+    const uint64_t t0 = global_ns();
+    for (;;) {
         v = *slot;
-        if ((uint32_t)(v >> 32) != want) {
-            const uint64_t t0 = global_ns();
-            for (;;) {
-                v = *slot;
-                if ((uint32_t)(v >> 32) == want) break;
-                if (ld_relaxed_i32(P.err) != 0) { good = 0; break; }
-                if ((long long)(global_ns() - t0) > P.wait_limit_ns) {
-                    raise_error(P.err, kEtimeout);
-                    good = 0;
-                    break;
-                }
-            }
+        if ((uint32_t)(v >> 32) == want) return (uint32_t)v;
+        if (ld_relaxed_i32(err) != 0) {
+            ok = false;
+            return 0;
+        }
+        if ((long long)(global_ns() - t0) > limit) {
+            raise_error(err, kEtimeout);
+            ok = false;
+            return 0;
         }
     }
-    ok = __shfl_sync(kFull, good, 0) != 0;
-    return __shfl_sync(kFull, (uint32_t)v, 0);
 }
 
-// One chunk of C columns for one lane: state (Sv, Yv) with V = Sv | Yv.
-// Returns the C carry-out bits.  `pmL` points at this lane's column of the
-// warp's match table.  RAGGED: only the first `valid` columns exist.
-template <int C, bool RAGGED>
-__device__ __forceinline__ uint32_t chunk_columns(uint32_t &Sv, uint32_t &Yv, uint32_t cin,
-                                                  const uint8_t *bq, bool aligned, int valid,
-                                                  const uint32_t *pmL) {
-    constexpr int NW = (C + 3) / 4;
-    uint32_t bw[NW];
-#pragma unroll
-    for (int k = 0; k < NW; ++k) bw[k] = 0;
-    bool vec = false;
-    if constexpr (C >= 4) {
-        if (!RAGGED && aligned) {
-            vec = true;
-            if constexpr (C == 4) {
-                bw[0] = __ldg(reinterpret_cast<const uint32_t *>(bq));
-            } else if constexpr (C == 8) {
-                const uint2 v = __ldg(reinterpret_cast<const uint2 *>(bq));
-                bw[0] = v.x;
-                bw[1] = v.y;
-            } else {
-#pragma unroll
-                for (int k = 0; k < NW; k += 4) {
-                    const uint4 v = __ldg(reinterpret_cast<const uint4 *>(bq) + k / 4);
-                    bw[k] = v.x;
-                    bw[k + 1] = v.y;
-                    bw[k + 2] = v.z;
-                    bw[k + 3] = v.w;
-                }
-            }
+// Lane 31 waits until the next warp has consumed ring word `need - 1`.
+__device__ __noinline__ bool wait_consumed(volatile int *cons, int need, int *err, long long limit) {
+    if (*cons >= need) return true;
+    const uint64_t t0 = global_ns();
+    while (*cons < need) {
+        if (ld_relaxed_i32(err) != 0) return false;
+        if ((long long)(global_ns() - t0) > limit) {
+            raise_error(err, kEtimeout);
+            return false;
         }
     }
-    if (!vec) {
-#pragma unroll
-        for (int jj = 0; jj < C; ++jj) {
-            if (!RAGGED || jj < valid) bw[jj >> 2] |= (uint32_t)__ldg(bq + jj) << ((jj & 3) * 8);
-        }
-    }
-    uint32_t cw = 0;
-#pragma unroll
-    for (int jj = 0; jj < C; ++jj) {
-        if (RAGGED && jj >= valid) break;
-        const uint32_t ch = (bw[jj >> 2] >> ((jj & 3) * 8)) & 0xffu;
-        const uint32_t M = pmL[ch << 5];
-        const uint32_t V = Sv | Yv;
-        const uint32_t X = V & M;
-        Yv = V & ~M;
-        const uint64_t sum = (uint64_t)V + X + ((cin >> jj) & 1u);
-        Sv = (uint32_t)sum;
-        cw |= (uint32_t)(sum >> 32) << jj;
-    }
-    return cw;
+    return true;
 }
+
+constexpr uint32_t kK31 = 0x7fffffffu;  // the 31 row bits of a lane word
+constexpr int kLaneRows = 31;
+
+__device__ __forceinline__ uint4 ldg_v4(const void *p) {
+    uint4 v;
+    asm volatile("ld.global.nc.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
+    return v;
+}
+
+// Shared-memory load at a 32-bit shared address.
+__device__ __forceinline__ uint32_t lds_u32(uint32_t addr) {
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
+    return v;
+}
+
+// One column of Eq. (1) on a lane's 31 rows, state (S, Y) with V = (S|Y) & K31.
+//   V = (S|Y) & K31, X = (S|Y) & M, Y' = (S|Y) & ~M        (three LOP3, one level)
+//   S' = V + X + c, with c the top bit of the shift register sr (add.cc)
+// V and X are below 2^31, so bit 31 of S' is the carry out of the lane's
+// bottom row; bit 31 of S and Y is never read (V and X mask it), and the
+// carry is shifted into cw (MSB first).
+__device__ __forceinline__ void column31(uint32_t &S, uint32_t &Y, uint32_t &sr, uint32_t &cw,
+                                         uint32_t M) {
+    uint32_t V, X, Yn, A;
+    asm("lop3.b32 %0, %1, %2, %3, 0xA8;" : "=r"(V) : "r"(S), "r"(Y), "r"(kK31));
+    asm("lop3.b32 %0, %1, %2, %3, 0xA8;" : "=r"(X) : "r"(S), "r"(Y), "r"(M));
+    asm("lop3.b32 %0, %1, %2, %3, 0x54;" : "=r"(Yn) : "r"(S), "r"(Y), "r"(M));
+    asm("{\n\t"
+        "add.cc.u32 %0, %0, %0;\n\t"
+        "addc.u32 %1, %2, %3;\n\t"
+        "}"
+        : "+r"(sr), "=r"(A)
+        : "r"(V), "r"(X));
+    S = A;
+    Y = Yn;
+    cw = __funnelshift_l(A, cw, 1);
+}
+
+// The 32 column offsets [col0, col0 + 32) of a lane's word; columns outside
+// [0, S) read as 0 (their steps are inactive).
+__device__ __forceinline__ void load_window(const uint32_t *boff, int64_t col0, int64_t S,
+                                            uint32_t (&w)[32]) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int64_t c = col0 + 4 * k;
+        if (c >= 0 && c + 4 <= S) {
+            const uint4 v = ldg_v4(boff + c);
+            w[4 * k] = v.x;
+            w[4 * k + 1] = v.y;
+            w[4 * k + 2] = v.z;
+            w[4 * k + 3] = v.w;
+        } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) w[4 * k + e] = (c + e >= 0 && c + e < S) ? __ldg(boff + c + e) : 0u;
+        }
+    }
+}
+
+// Lane skew in chunks: lane k works on chunk t - 2k at step t, so the
+// carry word a lane receives from the lane above (one __shfl_up_sync per
+// step) was produced a full step before it is needed.
+constexpr int kSkew = 2;
+// Input-word ring of warp 0 (pairs of tagged words) and its prefetch depth.
+constexpr int kSrcRing = 8;
+constexpr int kSrcAhead = 4;
 
 template <int C>
-__global__ void __launch_bounds__(1024) k_pair_bp(const PairArgs P) {
+__global__ void __launch_bounds__(256, 1) k_pair_bp(const PairArgs P) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_strip;
     const int W = blockDim.x >> 5;
@@ -177,14 +190,24 @@ __global__ void __launch_bounds__(1024) k_pair_bp(const PairArgs P) {
     uint64_t *ring_out = rings + (size_t)w * kRing;                       // read by warp w+1
     const uint64_t *ring_in = rings + (size_t)(w > 0 ? w - 1 : 0) * kRing;  // written by warp w-1
     volatile int *cons = reinterpret_cast<volatile int *>(rings + (size_t)W * kRing);
-    const uint32_t *pmL = pm + lane;
+    __shared__ __align__(16) uint64_t s_src[2 * kSrcRing];
+    const uint32_t src_ring = (uint32_t)__cvta_generic_to_shared(s_src);
+    const uint32_t pm_lane = (uint32_t)__cvta_generic_to_shared(pm + lane);
 
     for (int c = 0; c < kMaxSigma; ++c) pm[c * 32 + lane] = 0u;
 
-    const int64_t nch = P.nchunks;
+    constexpr int K = 32 / C;                      // steps per 32-column word
     constexpr uint32_t cmask = (C == 32) ? kFull : ((1u << C) - 1u);
-    const bool baligned = ((reinterpret_cast<uintptr_t>(P.b) & 15) == 0);
-    const int last_valid = (int)(P.S - (nch - 1) * C);  // columns in the last chunk
+    constexpr int kLag = kSkew * 31;               // chunks lane 31 trails lane 0
+    constexpr int kFlushStep = (kLag - 1) % K;     // step at which lane 31 completes a word
+    const int64_t nch = P.nchunks;
+    const int last_valid = (int)(P.S - (nch - 1) * C);
+    const int64_t nch_full = (last_valid == C) ? nch : nch - 1;
+    const int64_t nwords = P.nwords;
+    const int64_t nouter = (nch + kLag + K - 1) / K;
+    const int64_t u_fast0 = (kLag + K - 1) / K;
+    const int64_t u_fast1 = nch_full / K;           // exclusive
+    const int64_t lwords = (P.L + 31) >> 5;
 
     for (;;) {
         __syncthreads();
@@ -201,125 +224,191 @@ __global__ void __launch_bounds__(1024) k_pair_bp(const PairArgs P) {
 
         const int64_t row0 = P.strip_row0[s];
         const int64_t row1 = P.strip_row0[s + 1];
-        const int64_t rbase = row0 + (int64_t)w * kWarpRows + (int64_t)lane * 32;
+        const int64_t rbase = row0 + (int64_t)w * (32 * kLaneRows) + (int64_t)lane * kLaneRows;
         const int64_t left_rows = row1 - rbase;
-        const int nreal = left_rows <= 0 ? 0 : (left_rows >= 32 ? 32 : (int)left_rows);
-        const uint32_t realmask = nreal == 32 ? kFull : ((1u << nreal) - 1u);
+        const int nreal = left_rows <= 0 ? 0 : (left_rows >= kLaneRows ? kLaneRows : (int)left_rows);
+        const uint32_t realmask = (1u << nreal) - 1u;
 
-        // this lane's 32 row symbols and its match-table column
+        // this lane's 31 row symbols -> its column of the match table
         uint32_t aw[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) aw[k] = 0;
-        if (nreal == 32 && ((reinterpret_cast<uintptr_t>(P.a + rbase) & 15) == 0)) {
-            const uint4 v0 = __ldg(reinterpret_cast<const uint4 *>(P.a + rbase));
-            const uint4 v1 = __ldg(reinterpret_cast<const uint4 *>(P.a + rbase) + 1);
-            aw[0] = v0.x; aw[1] = v0.y; aw[2] = v0.z; aw[3] = v0.w;
-            aw[4] = v1.x; aw[5] = v1.y; aw[6] = v1.z; aw[7] = v1.w;
-        } else {
 #pragma unroll
-            for (int r = 0; r < 32; ++r)
-                if (r < nreal) aw[r >> 2] |= (uint32_t)__ldg(P.a + rbase + r) << ((r & 3) * 8);
-        }
+        for (int r = 0; r < kLaneRows; ++r)
+            if (r < nreal) aw[r >> 2] |= (uint32_t)__ldg(P.a + rbase + r) << ((r & 3) * 8);
 #pragma unroll
-        for (int r = 0; r < 32; ++r) {
+        for (int r = 0; r < kLaneRows; ++r) {
             if (r < nreal) {
                 const uint32_t ch = (aw[r >> 2] >> ((r & 3) * 8)) & 0xffu;
                 pm[ch * 32 + lane] |= 1u << r;
             }
         }
-        uint32_t Sv = kFull, Yv = 0;  // V = Sv | Yv; padding rows carry V bit 1
-        if (nreal > 0) Sv = (~__ldg(P.left_bits + (rbase >> 5))) | ~realmask;
+        // V from the first column's vertical steps (bit set = no step); padding rows 1
+        uint32_t Sv = kK31, Yv = 0;
+        if (nreal > 0) {
+            const int64_t wi = rbase >> 5;
+            const uint32_t lo = __ldg(P.left_bits + wi);
+            const uint32_t hi = (wi + 1 < lwords) ? __ldg(P.left_bits + wi + 1) : 0u;
+            const uint32_t steps = __funnelshift_r(lo, hi, (uint32_t)(rbase & 31)) & realmask;
+            Sv = (~steps) & kK31;
+        }
         __syncwarp();
 
-        const uint64_t *src_row = P.hbuf + (size_t)s * P.nwords;
-        uint64_t *dst_row = P.hbuf + (size_t)(s + 1) * P.nwords;
+        const uint64_t *src_row = P.hbuf + (size_t)s * P.hstride;
+        uint64_t *dst_row = P.hbuf + (size_t)(s + 1) * P.hstride;
         const uint32_t want = (s == P.stall_strip) ? (P.epoch ^ 0x80000000u) : P.epoch;
-        constexpr int kPrefetch = 4;  // words loaded ahead by warp 0
-        uint64_t win = 0;             // lane x holds input word x (mod 32)
-        if (w == 0 && lane <= kPrefetch && lane < P.nwords) win = ld_relaxed_u64(src_row + lane);
-        uint32_t curw = 0;
-        uint32_t cw_prev = 0;
-        uint32_t gw = 0;
+        // Warp 0, lane 0: the strip's input words arrive through a shared
+        // ring filled by cp.async two words at a time, kSrcAhead pairs ahead,
+        // so no register waits on an L2 round trip; a word whose tag is not
+        // yet the launch epoch (not yet published) is polled in global memory.
+        const int64_t npairs = (nwords + 1) >> 1;
+        auto issue_pair = [&](int64_t pr) {
+            if (pr < npairs) {
+                const uint32_t dst = src_ring + (uint32_t)((pr % kSrcRing) * 16);
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src_row + 2 * pr)
+                             : "memory");
+            }
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        };
+        if (w == 0 && lane == 0)
+            for (int d = 0; d < kSrcAhead; ++d) issue_pair(d);
+        uint64_t ring_pf = 0;       // warps w > 0, lane 0: next ring word
+        uint32_t cw_last = 0;       // this lane's carry-outs of the previous step
+        uint32_t cin_cur = 0;       // carry-ins for this step (from the lane above)
+        uint32_t gw = 0;            // lane 31: output word being assembled
+        uint32_t win[32], wnext[32];
         bool ok = true;
-        const int64_t nsteps = nch + 31;
-        for (int64_t t = 0; t < nsteps; ++t) {
-            const int64_t q = t - lane;
-            uint32_t cin = __shfl_up_sync(kFull, cw_prev, 1);
-            if (t < nch) {
-                uint32_t src;
+        bool bad31 = false;
+        load_window(P.boff, -(int64_t)kSkew * lane * C, P.S, win);
+        for (int64_t u = 0; u < nouter; ++u) {
+            uint32_t srcw = 0;
+            bool lok = !bad31;
+            if (lane == 0 && u < nwords) {
                 if (w == 0) {
-                    const int64_t bitpos = t * C;
-                    const int sh = (int)(bitpos & 31);
-                    if (sh == 0) {
-                        const int64_t wi = bitpos >> 5;
-                        const int64_t pf = wi + kPrefetch;
-                        if (pf < P.nwords && lane == (int)(pf & 31)) win = ld_relaxed_u64(src_row + pf);
-                        const uint32_t lo = __shfl_sync(kFull, (uint32_t)win, (int)(wi & 31));
-                        const uint32_t hi = __shfl_sync(kFull, (uint32_t)(win >> 32), (int)(wi & 31));
-                        if (hi != want) {
-                            const uint64_t v = poll_global(src_row + wi, want, P, ok);
-                            curw = (uint32_t)v;
-                        } else {
-                            curw = lo;
-                        }
+                    if ((u & 1) == 0) {
+                        asm volatile("cp.async.wait_group %0;" ::"n"(kSrcAhead - 1) : "memory");
+                        issue_pair((u >> 1) + kSrcAhead);
                     }
-                    src = (curw >> sh) & cmask;
+                    const uint32_t slot = src_ring + (uint32_t)((((u >> 1) % kSrcRing) * 16) + (u & 1) * 8);
+                    uint64_t v;
+                    asm volatile("ld.shared.u64 %0, [%1];" : "=l"(v) : "r"(slot) : "memory");
+                    if ((uint32_t)(v >> 32) != want)
+                        v = poll_global_lane(src_row + u, want, P.err, P.wait_limit_ns, lok);
+                    srcw = (uint32_t)v;
                 } else {
-                    src = poll_ring(ring_in, t, P, ok);
-                    if (lane == 0) cons[w] = (int)(t + 1);
+                    uint64_t v = ring_pf;
+                    if ((uint32_t)(v >> 32) != (uint32_t)(u + 1))
+                        v = poll_ring_lane(ring_in, u, P.err, P.wait_limit_ns, lok);
+                    srcw = (uint32_t)v;
+                    cons[w] = (int)(u + 1);
+                    if (u + 1 < nwords)
+                        ring_pf = reinterpret_cast<const volatile uint64_t *>(ring_in)[(u + 1) % kRing];
                 }
-                if (!ok) break;
-                if (lane == 0) cin = src;
             }
-            uint32_t cw = 0;
-            const bool act = (q >= 0) && (q < nch);
-            if (act) {
-                const uint8_t *bq = P.b + q * C;
-                if (q + 1 < nch || last_valid == C)
-                    cw = chunk_columns<C, false>(Sv, Yv, cin, bq, baligned, C, pmL);
-                else
-                    cw = chunk_columns<C, true>(Sv, Yv, cin, bq, baligned, last_valid, pmL);
+            if (!__all_sync(kFull, lok)) {
+                ok = false;
+                break;
             }
-            cw_prev = cw;
-            int bad = 0;
-            if (lane == 31 && act) {
-                if (w + 1 < W) {
-                    // the consumer (warp w+1) must have taken chunk q - kRing from this slot
-                    const int need = (int)(q - kRing + 1);
-                    if (cons[w + 1] < need) {
-                        const uint64_t t0 = global_ns();
-                        while (cons[w + 1] < need) {
-                            if (ld_relaxed_i32(P.err) != 0) { bad = 1; break; }
-                            if ((long long)(global_ns() - t0) > P.wait_limit_ns) {
-                                raise_error(P.err, kEtimeout);
-                                bad = 1;
-                                break;
+            const int64_t ubase = u * K;
+            const int64_t col0 = (ubase - (int64_t)kSkew * lane) * C;  // this lane's 32 columns
+            if (u + 1 < nouter) load_window(P.boff, col0 + 32, P.S, wnext);
+            if (u >= u_fast0 && u < u_fast1) {
+                // ---------- steady state: all lanes hold full chunks ----------
+#pragma unroll
+                for (int i = 0; i < K; ++i) {
+                    const uint32_t recv = __shfl_up_sync(kFull, cw_last, 1);
+                    uint32_t sr = (lane == 0) ? (srcw << (i * C)) : (cin_cur << (32 - C));
+                    uint32_t cw = 0;
+#pragma unroll
+                    for (int jj = 0; jj < C; ++jj) {
+                        const uint32_t M = lds_u32(pm_lane + win[i * C + jj]);
+                        column31(Sv, Yv, sr, cw, M);
+                    }
+                    cw_last = cw;
+                    cin_cur = recv;
+                    gw |= cw << ((32 - C - (((i + kSkew) * C) & 31)) & 31);
+                    if (i == kFlushStep) {
+                        if (lane == 31) {
+                            const int64_t wq = ((ubase + i - kLag) * C) >> 5;
+                            if (w + 1 < W) {
+                                if (!wait_consumed(cons + w + 1, (int)(wq - kRing + 1), P.err, P.wait_limit_ns))
+                                    bad31 = true;
+                                reinterpret_cast<volatile uint64_t *>(ring_out)[wq % kRing] =
+                                    ((uint64_t)(uint32_t)(wq + 1) << 32) | gw;
+                            } else {
+                                st_relaxed_u64(dst_row + wq, ((uint64_t)P.epoch << 32) | gw);
                             }
                         }
-                    }
-                    reinterpret_cast<volatile uint64_t *>(ring_out)[q % kRing] =
-                        ((uint64_t)(uint32_t)(q + 1) << 32) | cw;
-                } else {
-                    const int sh = (int)((q * C) & 31);
-                    gw |= cw << sh;
-                    if (sh + C == 32 || q == nch - 1) {
-                        st_relaxed_u64(dst_row + ((q * C) >> 5), ((uint64_t)P.epoch << 32) | gw);
                         gw = 0;
                     }
                 }
-            }
-            if (__any_sync(kFull, bad)) { ok = false; break; }
-        }
-
-        if (ok && nreal > 0) P.right_bits[rbase >> 5] = ~(Sv | Yv) & realmask;
+            } else {
+                // ---------- fill / drain: the same windows, per-lane activity ----------
 #pragma unroll
-        for (int r = 0; r < 32; ++r) {
+                for (int i = 0; i < K; ++i) {
+                    const int64_t q = ubase + i - (int64_t)kSkew * lane;
+                    const uint32_t recv = __shfl_up_sync(kFull, cw_last, 1);
+                    uint32_t sr = (lane == 0) ? (srcw << (i * C)) : (cin_cur << (32 - C));
+                    uint32_t cw = 0;
+                    const bool act = (q >= 0) && (q < nch);
+                    if (act) {
+                        if (q == nch - 1 && last_valid < C) {
+#pragma unroll
+                            for (int jj = 0; jj < C; ++jj) {
+                                if (jj < last_valid) {
+                                    const uint32_t M = lds_u32(pm_lane + win[i * C + jj]);
+                                    column31(Sv, Yv, sr, cw, M);
+                                }
+                            }
+                            cw <<= (C - last_valid);  // keep the chunk MSB-first
+                        } else {
+#pragma unroll
+                            for (int jj = 0; jj < C; ++jj) {
+                                const uint32_t M = lds_u32(pm_lane + win[i * C + jj]);
+                                column31(Sv, Yv, sr, cw, M);
+                            }
+                        }
+                    }
+                    cw_last = cw;
+                    cin_cur = recv;
+                    if (lane == 31 && act) {
+                        gw |= cw << (32 - C - ((q * C) & 31));
+                        if (i == kFlushStep || q == nch - 1) {
+                            const int64_t wq = (q * C) >> 5;
+                            if (w + 1 < W) {
+                                if (!wait_consumed(cons + w + 1, (int)(wq - kRing + 1), P.err, P.wait_limit_ns))
+                                    bad31 = true;
+                                reinterpret_cast<volatile uint64_t *>(ring_out)[wq % kRing] =
+                                    ((uint64_t)(uint32_t)(wq + 1) << 32) | gw;
+                            } else {
+                                st_relaxed_u64(dst_row + wq, ((uint64_t)P.epoch << 32) | gw);
+                            }
+                            gw = 0;
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 32; ++k) win[k] = wnext[k];
+        }
+        if (w == 0 && lane == 0) asm volatile("cp.async.wait_all;" ::: "memory");
+
+        if (ok && nreal > 0) P.right_bits[rbase / kLaneRows] = ~(Sv | Yv) & realmask;
+#pragma unroll
+        for (int r = 0; r < kLaneRows; ++r) {
             if (r < nreal) {
                 const uint32_t ch = (aw[r >> 2] >> ((r & 3) * 8)) & 0xffu;
                 pm[ch * 32 + lane] = 0u;
             }
         }
     }
+}
+
+// Column string -> byte offsets of its symbols' rows in a warp's match table.
+__global__ void k_column_offsets(const uint8_t *b, int64_t S, uint32_t *boff) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < S;
+         j += (int64_t)gridDim.x * blockDim.x)
+        boff[j] = (uint32_t)b[j] * 32u * 4u;
 }
 
 // ---------------------------------------------------------------------------
@@ -349,7 +438,7 @@ __global__ void k_boundary_bits(const int32_t *v, int64_t len, uint32_t *bits, u
         }
         if (badstep) atomicCAS(err, 0, kEinval);
         if (bits) bits[k] = word;
-        if (tagged) tagged[k] = ((uint64_t)epoch << 32) | word;
+        if (tagged) tagged[k] = ((uint64_t)epoch << 32) | __brev(word);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0 && other != nullptr && other[0] != v[0])
         atomicCAS(err, 0, kEinval);
@@ -365,19 +454,20 @@ __global__ void k_tag_zero(uint64_t *tagged, int64_t nw, uint32_t epoch) {
 constexpr int kPB = 1024;
 
 __device__ __forceinline__ uint32_t load_bits_word(const uint32_t *bits, const uint64_t *tagged,
-                                                   int64_t k) {
-    return bits ? bits[k] : (uint32_t)tagged[k];
+                                                   int64_t k) {  // tagged words are MSB-first columns
+    return bits ? bits[k] : __brev((uint32_t)tagged[k]);
 }
 
+template <int BPW>
 __global__ void k_prefix_pass1(const uint32_t *bits, const uint64_t *tagged, int64_t nbits,
                                int64_t *block_sums) {
     __shared__ int64_t red[32];
-    const int64_t nw = (nbits + 31) >> 5;
+    const int64_t nw = (nbits + BPW - 1) / BPW;
     const int64_t k = blockIdx.x * (int64_t)kPB + threadIdx.x;
     uint32_t c = 0;
     if (k < nw) {
         uint32_t word = load_bits_word(bits, tagged, k);
-        const int64_t rem = nbits - k * 32;
+        const int64_t rem = nbits - k * BPW;
         if (rem < 32) word &= (1u << rem) - 1u;
         c = __popc(word);
     }
@@ -427,19 +517,21 @@ __global__ void k_prefix_pass2(int64_t *block_sums, int64_t nblocks) {
 }
 
 // Pass 3: out[0] = base; out[i+1] = base + (number of set bits among the first i+1).
+// A word holds BPW elements (32 for packed bit rows, 31 for lane words).
+template <int BPW>
 __global__ void k_prefix_pass3(const uint32_t *bits, const uint64_t *tagged, int64_t nbits,
                                const int64_t *block_excl, const int32_t *base_ptr,
                                int64_t base_index, int32_t *out, int32_t *len_out) {
     __shared__ uint32_t words[kPB];
     __shared__ int32_t wpre[kPB];
     __shared__ int32_t warp_tot[32];
-    const int64_t nw = (nbits + 31) >> 5;
+    const int64_t nw = (nbits + BPW - 1) / BPW;
     const int64_t k0 = blockIdx.x * (int64_t)kPB;
     const int64_t k = k0 + threadIdx.x;
     uint32_t word = 0;
     if (k < nw) {
         word = load_bits_word(bits, tagged, k);
-        const int64_t rem = nbits - k * 32;
+        const int64_t rem = nbits - k * BPW;
         if (rem < 32) word &= (1u << rem) - 1u;
     }
     words[threadIdx.x] = word;
@@ -463,15 +555,16 @@ __global__ void k_prefix_pass3(const uint32_t *bits, const uint64_t *tagged, int
     __syncthreads();
     wpre[threadIdx.x] = warp_tot[threadIdx.x >> 5] + inc - c;
     __syncthreads();
-    const int32_t base = (base_ptr ? base_ptr[base_index] : 0) + (int32_t)block_excl[blockIdx.x];
+    const int32_t base0 = base_ptr ? base_ptr[base_index] : 0;
+    const int32_t base = base0 + (int32_t)block_excl[blockIdx.x];
     if (out != nullptr) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) out[0] = base_ptr ? base_ptr[base_index] : 0;
-        const int64_t nb_here = min((int64_t)kPB * 32, nbits - k0 * 32);
+        if (blockIdx.x == 0 && threadIdx.x == 0) out[0] = base0;
+        const int64_t nb_here = min((int64_t)kPB * BPW, nbits - k0 * BPW);
         for (int64_t idx = threadIdx.x; idx < nb_here; idx += blockDim.x) {
-            const int wl = (int)(idx >> 5);
-            const int b = (int)(idx & 31);
+            const int wl = (int)(idx / BPW);
+            const int b = (int)(idx - (int64_t)wl * BPW);
             const uint32_t mask = b == 31 ? kFull : ((2u << b) - 1u);
-            out[k0 * 32 + idx + 1] = base + wpre[wl] + __popc(words[wl] & mask);
+            out[k0 * BPW + idx + 1] = base + wpre[wl] + __popc(words[wl] & mask);
         }
     }
     if (len_out != nullptr && blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
@@ -584,7 +677,6 @@ static int occ_c(int warps) {
 
 int pair_occupancy(int C, int warps) {
     switch (C) {
-        case 1: return occ_c<1>(warps);
         case 2: return occ_c<2>(warps);
         case 4: return occ_c<4>(warps);
         case 8: return occ_c<8>(warps);
@@ -596,7 +688,6 @@ int pair_occupancy(int C, int warps) {
 
 cudaError_t launch_pair_bp(const PairArgs &p, int C, int warps, int grid, cudaStream_t st) {
     switch (C) {
-        case 1: return launch_c<1>(p, warps, grid, st);
         case 2: return launch_c<2>(p, warps, grid, st);
         case 4: return launch_c<4>(p, warps, grid, st);
         case 8: return launch_c<8>(p, warps, grid, st);
@@ -630,16 +721,29 @@ cudaError_t launch_boundary_bits(const int32_t *v, int64_t len, uint32_t *bits, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_bits_prefix(const uint32_t *bits, const uint64_t *tagged, int64_t nbits,
+cudaError_t launch_bits_prefix(const uint32_t *bits, const uint64_t *tagged, int64_t nbits, int bpw,
                                const int32_t *base_ptr, int64_t base_index, int32_t *out,
                                int32_t *len_out, PrefixScratch &scr, cudaStream_t st) {
-    const int64_t nw = (nbits + 31) >> 5;
+    const int64_t nw = (nbits + bpw - 1) / bpw;
     const int64_t nblocks = (nw + kPB - 1) / kPB;
-    if (nblocks == 0 || nblocks > scr.cap) return cudaErrorInvalidValue;
-    k_prefix_pass1<<<(unsigned)nblocks, kPB, 0, st>>>(bits, tagged, nbits, scr.block_sums);
-    k_prefix_pass2<<<1, 1024, 0, st>>>(scr.block_sums, nblocks);
-    k_prefix_pass3<<<(unsigned)nblocks, kPB, 0, st>>>(bits, tagged, nbits, scr.block_sums, base_ptr,
-                                                      base_index, out, len_out);
+    if (nblocks == 0 || nblocks > scr.cap || (bpw != 31 && bpw != 32)) return cudaErrorInvalidValue;
+    if (bpw == 32) {
+        k_prefix_pass1<32><<<(unsigned)nblocks, kPB, 0, st>>>(bits, tagged, nbits, scr.block_sums);
+        k_prefix_pass2<<<1, 1024, 0, st>>>(scr.block_sums, nblocks);
+        k_prefix_pass3<32><<<(unsigned)nblocks, kPB, 0, st>>>(bits, tagged, nbits, scr.block_sums,
+                                                              base_ptr, base_index, out, len_out);
+    } else {
+        k_prefix_pass1<31><<<(unsigned)nblocks, kPB, 0, st>>>(bits, tagged, nbits, scr.block_sums);
+        k_prefix_pass2<<<1, 1024, 0, st>>>(scr.block_sums, nblocks);
+        k_prefix_pass3<31><<<(unsigned)nblocks, kPB, 0, st>>>(bits, tagged, nbits, scr.block_sums,
+                                                              base_ptr, base_index, out, len_out);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_column_offsets(const uint8_t *b, int64_t S, uint32_t *boff, cudaStream_t st) {
+    const int grid = (int)min((int64_t)4096, (S + 255) / 256);
+    k_column_offsets<<<grid, 256, 0, st>>>(b, S, boff);
     return cudaGetLastError();
 }
 

@@ -86,12 +86,15 @@ int run_pair(paco_ctx *ctx, const uint8_t *a, int64_t n, const uint8_t *b, int64
     int32_t *kright = pl.transpose ? bottom_row : right_col;
 
     const int64_t nwords = (S + 31) / 32;
+    const int64_t hstride = (nwords + 1) & ~(int64_t)1;
     const int64_t lwords = (L + 31) / 32;
+    const int64_t rwords = (L + 30) / 31;
     const int64_t maxbits = std::max(L, S);
-    const int64_t nblocks = ((maxbits + 31) / 32 + 1023) / 1024 + 1;
-    if ((rc = ensure_bytes(ctx, ctx->hbuf, (size_t)(pl.nstrips + 1) * nwords * 8)) != PACO_OK) return rc;
+    const int64_t nblocks = ((maxbits + 30) / 31 + 1023) / 1024 + 1;
+    if ((rc = ensure_bytes(ctx, ctx->hbuf, (size_t)(pl.nstrips + 1) * hstride * 8 + 16)) != PACO_OK) return rc;
     if ((rc = ensure_bytes(ctx, ctx->lbits, (size_t)lwords * 4 + 16)) != PACO_OK) return rc;
-    if ((rc = ensure_bytes(ctx, ctx->rbits, (size_t)lwords * 4 + 16)) != PACO_OK) return rc;
+    if ((rc = ensure_bytes(ctx, ctx->rbits, (size_t)rwords * 4 + 16)) != PACO_OK) return rc;
+    if ((rc = ensure_bytes(ctx, ctx->boff, (size_t)S * 4 + 64)) != PACO_OK) return rc;
     if ((rc = ensure_bytes(ctx, ctx->sums, (size_t)nblocks * 8 * 2)) != PACO_OK) return rc;
 
     const uint32_t epoch = next_epoch(ctx);
@@ -100,16 +103,19 @@ int run_pair(paco_ctx *ctx, const uint8_t *a, int64_t n, const uint8_t *b, int64
                              ctx->err_ptr(), st);
     if (e == cudaSuccess)
         e = launch_boundary_bits(ktop, S, nullptr, hbuf, epoch, kleft, ctx->err_ptr(), st);
+    if (e == cudaSuccess) e = launch_column_offsets(kb, S, (uint32_t *)ctx->boff.ptr, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ticket_ptr(), 0, sizeof(int), st);
     if (e != cudaSuccess) return set_cuda_error(ctx, e, "prepare boundaries");
 
     PairArgs P;
     P.a = ka;
     P.b = kb;
+    P.boff = (const uint32_t *)ctx->boff.ptr;
     P.L = L;
     P.S = S;
     P.nchunks = (S + pl.C - 1) / pl.C;
     P.nwords = nwords;
+    P.hstride = hstride;
     P.strip_row0 = (const int64_t *)cp->d_row0.ptr;
     P.nstrips = pl.nstrips;
     P.sigma = kMaxSigma;
@@ -130,12 +136,12 @@ int run_pair(paco_ctx *ctx, const uint8_t *a, int64_t n, const uint8_t *b, int64
 
     PrefixScratch scr{(int64_t *)ctx->sums.ptr, nblocks};
     // kernel bottom row: the last strip's carries (tagged row nstrips), base H[L][0] = kleft[L]
-    e = launch_bits_prefix(nullptr, hbuf + (size_t)pl.nstrips * nwords, S, kleft, L, kbottom,
+    e = launch_bits_prefix(nullptr, hbuf + (size_t)pl.nstrips * hstride, S, 32, kleft, L, kbottom,
                            len, scr, st);
     if (e == cudaSuccess && kright != nullptr) {
         PrefixScratch scr2{(int64_t *)ctx->sums.ptr + nblocks, nblocks};
         // kernel right column: vertical steps of the last column, base H[0][S] = ktop[S]
-        e = launch_bits_prefix((const uint32_t *)ctx->rbits.ptr, nullptr, L, ktop, S, kright,
+        e = launch_bits_prefix((const uint32_t *)ctx->rbits.ptr, nullptr, L, 31, ktop, S, kright,
                                nullptr, scr2, st);
     }
     if (e != cudaSuccess) return set_cuda_error(ctx, e, "boundary prefixes");

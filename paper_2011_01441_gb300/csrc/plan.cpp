@@ -171,22 +171,24 @@ bool plan_pair(int64_t n, int64_t m, int sms, const PairPlanOptions &o, PairPlan
     out.transpose = o.orient == 2 || (o.orient == 0 && m > n);
     out.L = out.transpose ? m : n;
     out.S = out.transpose ? n : m;
-    // chunk width: minimise (S/C + L/32) * (C*c_col + c_hop), the critical path of the
-    // lane pipeline (c_col ~ cycles of one dependent column step, c_hop ~ a shuffle hop)
+    // chunk width: minimise the critical path of the lane pipeline, (S + 2*C*lanes) column
+    // steps of ~c_col cycles plus ~c_step cycles of per-chunk overhead (the carry hand-off
+    // through a shuffle is hidden behind one chunk by the two-chunk lane skew)
     if (o.chunk) {
         out.C = o.chunk;
     } else {
-        const double c_col = 9.0, c_hop = 25.0;
+        const double c_col = 8.0, c_step = 12.0;
+        const double lanes = (double)out.L / kPlanLaneRows;
         double best = 1e300;
-        for (int C = 1; C <= 32; C *= 2) {
-            const double cost = ((double)out.S / C + (double)out.L / 32.0) * (C * c_col + c_hop);
+        for (int C = 2; C <= 32; C *= 2) {
+            const double cost = ((double)out.S + 2.0 * C * lanes) * c_col + ((double)out.S / C + 2.0 * lanes) * c_step;
             if (cost < best) {
                 best = cost;
                 out.C = C;
             }
         }
     }
-    const int64_t warps_total = (out.L + 1023) / 1024;
+    const int64_t warps_total = (out.L + kPlanWarpRows - 1) / kPlanWarpRows;
     int W = o.warps > 0 ? o.warps : 4;
     W = std::max(1, std::min(W, o.max_warps));
     if ((int64_t)W > warps_total) W = (int)warps_total;
@@ -201,21 +203,21 @@ bool plan_pair(int64_t n, int64_t m, int sms, const PairPlanOptions &o, PairPlan
     }
     out.W = W;
     if (o.schedule == 1) {
-        const int64_t h = (int64_t)W * 1024;
+        const int64_t h = (int64_t)W * kPlanWarpRows;
         nstrips = (out.L + h - 1) / h;
         out.row0.resize((size_t)nstrips + 1);
         for (int64_t k = 0; k <= nstrips; ++k) out.row0[(size_t)k] = std::min(out.L, k * h);
     } else {
         // the p-way first division of the PACO partition on rows, p = nstrips,
-        // in 32-row granules (parts differ by at most one granule)
-        const int64_t G = (out.L + 31) / 32;
+        // in lane granules of 31 rows (parts differ by at most one granule)
+        const int64_t G = (out.L + kPlanLaneRows - 1) / kPlanLaneRows;
         const std::vector<int64_t> parts = balanced_split(G, nstrips);
         out.row0.resize((size_t)nstrips + 1);
         int64_t acc = 0;
         out.row0[0] = 0;
         for (int64_t k = 0; k < nstrips; ++k) {
             acc += parts[(size_t)k];
-            out.row0[(size_t)k + 1] = std::min(out.L, acc * 32);
+            out.row0[(size_t)k + 1] = std::min(out.L, acc * kPlanLaneRows);
         }
     }
     out.nstrips = (int)nstrips;

@@ -9,6 +9,11 @@
 
 namespace paco {
 
+// Rows held by one lane of the bit-parallel tile (bit 31 is its carry slot)
+// and by one warp of 32 lanes.
+constexpr int64_t kPlanLaneRows = 31;
+constexpr int64_t kPlanWarpRows = 31 * 32;
+
 // ---- the paper's partition, re-derived for an n x m table and any p ----
 //
 // Step 1 (the proof's simplification, "the first step of partitioning makes
@@ -45,14 +50,14 @@ struct PairPlan {
     int nstrips = 1;         // CTA strips (the p of the balanced split)
     int grid = 1;            // CTAs launched (<= nstrips)
     int64_t L = 0, S = 0;    // kernel rows (bit dimension) and streamed columns
-    std::vector<int64_t> row0;  // nstrips+1 offsets, multiples of 32, row0[nstrips] = L
+    std::vector<int64_t> row0;  // nstrips+1 offsets, multiples of 31, row0[nstrips] = L
 };
 
 struct PairPlanOptions {
     int chunk = 0;      // 0: cost model
     int warps = 0;      // 0: default
     int orient = 0;     // 0: bits along the longer string; 1: along a; 2: along b
-    int schedule = 0;   // 0: balanced strips (p-way split); 1: uniform strips of W*1024 rows
+    int schedule = 0;   // 0: balanced strips (p-way split); 1: uniform strips of W*992 rows
     int max_warps = 7;  // shared-memory limit per CTA
     int resident = 0;   // CTAs that fit on the device at once (0: unknown)
 };

@@ -161,14 +161,14 @@ def test_pair_plan_balanced_strips(lib, n, m, sms):
     row0 = pl["row0"]
     assert row0[0] == 0 and row0[-1] == L
     h = np.diff(row0)
-    assert np.all(h > 0) and np.all(row0[:-1] % 32 == 0)
-    assert np.all(h <= pl["warps"] * 1024)
+    assert np.all(h > 0) and np.all(row0[:-1] % 31 == 0)
+    assert np.all(h <= pl["warps"] * 992)
     if h.size > 2:
-        assert h[:-1].max() - h[:-1].min() <= 32  # the +-1 granule split of the p-way division
-    assert pl["chunk"] in (1, 2, 4, 8, 16, 32)
+        assert h[:-1].max() - h[:-1].min() <= 31  # the +-1 granule split of the p-way division
+    assert pl["chunk"] in (2, 4, 8, 16, 32)
 
 
 def test_pair_plan_options(lib):
     pl = P.paco_plan_pair(5000, 7000, 152, chunk=4, warps=2, orient=1, schedule=1)
     assert pl["transpose"] == 0 and pl["chunk"] == 4 and pl["warps"] == 2
-    assert list(pl["row0"]) == [0, 2048, 4096, 5000]
+    assert list(pl["row0"]) == [0, 1984, 3968, 5000]

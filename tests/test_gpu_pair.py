@@ -66,7 +66,7 @@ def test_alphabets(ctx, sigma):
     check(ctx, a, b)
 
 
-@pytest.mark.parametrize("chunk,warps", [(c, w) for c in (1, 2, 4, 8, 16, 32) for w in (1, 3)] + [(8, 7), (4, 2)])
+@pytest.mark.parametrize("chunk,warps", [(c, w) for c in (2, 4, 8, 16, 32) for w in (1, 3)] + [(8, 7), (4, 2)])
 def test_chunks_and_strip_heights(ctx, chunk, warps):
     # several CTA strips (inter-CTA chaining) and several warps (shared ring)
     a = W.symbols(chunk * 100 + warps, 0, 7000, 4)
@@ -99,7 +99,7 @@ def test_input_boundaries_from_a_real_table(ctx):
         H = oracle.lcs_table(np.concatenate([pa, a]), np.concatenate([pb, b]))
         top = H[pa.size, pb.size:].copy()
         left = H[pa.size:, pb.size].copy()
-        check(ctx, a, b, top, left, warps=1 + t % 3, chunk=[1, 4, 8][t % 3])
+        check(ctx, a, b, top, left, warps=1 + t % 3, chunk=[2, 4, 8][t % 3])
 
 
 def test_composition_chained_calls(ctx):
