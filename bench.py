@@ -34,7 +34,7 @@ from paper_2011_01441_gb300 import workloads as W  # noqa: E402
 
 METRIC = "LCS GCUPS on 1 GB300, % of INT32 roofline; served p50/p99 latency vs plain"
 # lane-ops per 32-row column step of the bit-parallel tile (or, and, and-not, add-with-carry)
-OPS_PER_WORD_STEP = 4
+OPS_PER_WORD_STEP = 4  # per 31-row lane word and column
 
 
 def _dist():
@@ -268,17 +268,163 @@ def run_gpu(args):
     ctx.close()
 
 
+def run_batch_bench(args):
+    """The 4096-pair batch through paco_lcs_batch (one graph replay per step)
+    against the single-pair path called once per pair."""
+    import torch
+    import paper_2011_01441_gb300 as P
+    P.load()
+    ctx = P.Context(0)
+    bt = W.batch_pairs()
+    da = torch.from_numpy(bt.a_cat).cuda()
+    db = torch.from_numpy(bt.b_cat).cuda()
+    L = torch.empty(bt.npairs, dtype=torch.int32, device="cuda")
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):  # the first call plans, autotunes and captures the graph
+        P.paco_lcs_batch(ctx, da, db, bt.a_off, bt.b_off, lengths=L)
+    ctx.sync()
+    ms = []
+    with ClockSampler(0) as clocks:
+        for _ in range(args.steps):
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            P.paco_lcs_batch(ctx, da, db, bt.a_off, bt.b_off, lengths=L)
+            e1.record()
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+    ctx.sync()
+    cells = bt.cells()
+    value = cells * args.steps / (sum(ms) * 1e-3) / 1e9
+    # plain: one pair per launch on one stream, same pairs
+    lens = torch.empty(1, dtype=torch.int32, device="cuda")
+    views = [(da[bt.a_off[k]:bt.a_off[k + 1]], db[bt.b_off[k]:bt.b_off[k + 1]]) for k in range(bt.npairs)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for a, b in views:
+        P.paco_lcs_length(ctx, a, b, out=lens)
+    torch.cuda.synchronize()
+    plain_s = time.perf_counter() - t0
+    peak_ops = P.paco_measure_int_peak(ctx, 0)
+    med = statistics.median(ms)
+    word_steps = sum(((max(n, m) + 30) // 31) * min(n, m) for n, m in zip(np.diff(bt.a_off), np.diff(bt.b_off)))
+    achieved = word_steps * OPS_PER_WORD_STEP / (med * 1e-3)
+    line = {"metric": METRIC, "value": value, "unit": "GCUPS", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": sum(ms) / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": bt.name + " (seed 4)", "pairs": bt.npairs, "cells": cells,
+                       "engine": "batch graph, warp jobs", "l2": "flushed between timed steps"},
+            "plain_one_pair_per_launch": {"value": cells / plain_s / 1e9, "unit": "GCUPS",
+                                          "seconds": plain_s},
+            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
+                         "unit": "Tops/s (int32 lane-ops)", "frac": achieved / peak_ops,
+                         "kernel": "k_batch", "ops_per_cell": OPS_PER_WORD_STEP / 31,
+                         "peak_source": "measured: paco_measure_int_peak(op=0), full-rate IADD3 on all SMs"},
+            "clocks": clocks.summary()}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def run_serve_bench(args):
+    """Poisson stream of requests through paco_lcs_submit / paco_lcs_poll at
+    fractions of the saturating rate; p50/p99 latency beside throughput, and
+    the same arrival schedule served one pair per launch (FIFO) as the plain
+    comparison."""
+    import threading as th
+    import torch
+    import paper_2011_01441_gb300 as P
+    P.load()
+    ctx = P.Context(0, mem_budget_bytes=8 << 30)
+    nreq = args.requests
+    reqs = [W.serve_request(k) for k in range(nreq)]
+    cells = np.array([r.a.size * r.b.size for r in reqs], dtype=np.float64)
+    # saturating rate from the batch path on this mix
+    a_cat = np.concatenate([r.a for r in reqs]); b_cat = np.concatenate([r.b for r in reqs])
+    a_off = np.concatenate([[0], np.cumsum([r.a.size for r in reqs])]).astype(np.int64)
+    b_off = np.concatenate([[0], np.cumsum([r.b.size for r in reqs])]).astype(np.int64)
+    da, db = torch.from_numpy(a_cat).cuda(), torch.from_numpy(b_cat).cuda()
+    P.paco_lcs_batch(ctx, da, db, a_off, b_off)
+    ctx.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(); P.paco_lcs_batch(ctx, da, db, a_off, b_off); e1.record(); e1.synchronize()
+    sat_gcups = cells.sum() / (e0.elapsed_time(e1) * 1e-3) / 1e9
+    lam_sat = sat_gcups * 1e9 / cells.mean()
+    results = {}
+    for frac in (0.5, 0.9, 1.0):
+        lam = frac * lam_sat
+        arr = W.poisson_arrivals(7, nreq, lam)
+        tickets = [None] * nreq
+        done_t = [None] * nreq
+        t_start = time.perf_counter()
+
+        def submitter():
+            for k in range(nreq):
+                delay = arr[k] - (time.perf_counter() - t_start)
+                if delay > 0:
+                    time.sleep(delay)
+                tickets[k] = P.paco_lcs_submit(ctx, reqs[k].a, reqs[k].b)
+        thr = th.Thread(target=submitter)
+        thr.start()
+        pending = set(range(nreq))
+        while pending:
+            for k in list(pending):
+                if tickets[k] is None:
+                    continue
+                r = P.paco_lcs_poll(ctx, tickets[k])
+                if r is not None:
+                    done_t[k] = time.perf_counter() - t_start
+                    pending.discard(k)
+            time.sleep(0.0002)
+        thr.join()
+        lat = np.array(done_t) - arr
+        wall = max(done_t) - arr[0]
+        results[f"{frac:.1f}"] = {"rate_per_s": lam, "gcups": cells.sum() / wall / 1e9,
+                                  "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                                  "p99_ms": float(np.percentile(lat, 99) * 1e3)}
+    # plain: FIFO, one pair per launch, same arrivals at 0.9 of saturation
+    arr = W.poisson_arrivals(7, nreq, 0.9 * lam_sat)
+    service = []
+    out = torch.empty(1, dtype=torch.int32, device="cuda")
+    for r in reqs:
+        a = torch.from_numpy(r.a).cuda(); b = torch.from_numpy(r.b).cuda()
+        torch.cuda.synchronize(); t0 = time.perf_counter()
+        P.paco_lcs_length(ctx, a, b, out=out); torch.cuda.synchronize()
+        service.append(time.perf_counter() - t0)
+    fin, lat_plain = 0.0, []
+    for k in range(nreq):
+        fin = max(fin, arr[k]) + service[k]
+        lat_plain.append(fin - arr[k])
+    lat_plain = np.array(lat_plain)
+    line = {"metric": METRIC, "value": results["1.0"]["gcups"], "unit": "GCUPS", "n_gpus": 1,
+            "steps": 1, "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u32", "data": "synthetic",
+            "config": {"workload": f"serving stream: {nreq} requests of the 100000-request mix (seed 5), lengths log-uniform [32, 65536], sigma 20, half 20%-mutated",
+                       "budget_bytes": 8 << 30, "saturating_rate_per_s": lam_sat,
+                       "batch_gcups_on_mix": sat_gcups},
+            "served": results,
+            "plain_fifo_one_pair_per_launch_at_0.9": {"gcups": cells.sum() / sum(service) / 1e9,
+                                                      "p50_ms": float(np.percentile(lat_plain, 50) * 1e3),
+                                                      "p99_ms": float(np.percentile(lat_plain, 99) * 1e3)}}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="mutated", choices=["mutated", "small", "skinny"])
+    ap.add_argument("--config", default="mutated", choices=["mutated", "small", "skinny", "batch", "serve"])
+    ap.add_argument("--requests", type=int, default=3000, help="serving: requests taken from the stream")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.config == "batch":
+        run_batch_bench(args)
+    elif args.config == "serve":
+        run_serve_bench(args)
     else:
         run_gpu(args)
 

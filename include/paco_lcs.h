@@ -132,23 +132,28 @@ int paco_lcs_boundaries_host(paco_ctx *ctx, const uint8_t *a, int64_t n,
 
 /* ---- batch of independent pairs ---------------------------------------- */
 
-/* npairs independent pairs in one persistent launch (captured once into a
- * CUDA graph per context and size-class layout, then replayed).
- *   a_cat, b_cat : device uint8, all strings concatenated
- *   a_off, b_off : device int64[npairs+1], string k is [off[k], off[k+1])
- *   d_len        : device int32[npairs]
- *   d_rows_cat   : device int32, row k at row_off[k] with m_k+1 entries (or NULL)
- *   row_off      : device int64[npairs] (ignored when d_rows_cat is NULL)
- *   d_cols_cat   : device int32, column k at col_off[k] with n_k+1 entries (or NULL)
- *   col_off      : device int64[npairs]
- * The host also needs the pair lengths to plan: h_a_off / h_b_off are the
- * same offsets in HOST memory (int64[npairs+1]).  Errors: PACO_EINVAL,
+/* npairs independent pairs in one persistent launch.  The whole step (column
+ * tables, the persistent warp-job kernel, the boundary prefixes) is captured
+ * once into a CUDA graph per context, layout and output pointers, then
+ * replayed; the chunk width is autotuned once per layout (PACO_OPT_CHUNK
+ * forces one).
+ *   a_cat, b_cat      : device uint8, all strings concatenated
+ *   h_a_off, h_b_off  : HOST int64[npairs+1]; pair k is a_cat[h_a_off[k] ..
+ *                       h_a_off[k+1]) x b_cat[h_b_off[k] .. h_b_off[k+1])
+ *   d_len             : device int32[npairs], receives L_k
+ *   d_rows_cat        : device int32 or NULL; pair k's bottom row H[n_k][0..m_k]
+ *                       (m_k+1 values) at offset h_row_off[k]
+ *   h_row_off         : HOST int64[npairs] (ignored when d_rows_cat is NULL)
+ *   d_cols_cat        : device int32 or NULL; pair k's right column
+ *                       H[0..n_k][m_k] (n_k+1 values) at offset h_col_off[k]
+ *   h_col_off         : HOST int64[npairs]
+ * The host arrays are read during the call (the planner needs the lengths).
+ * Errors: PACO_EINVAL (negative or oversized length, NULL with work to do),
  * PACO_ENOMEM, PACO_EDEVICE. */
-int paco_lcs_batch(paco_ctx *ctx, const uint8_t *a_cat, const int64_t *a_off,
-                   const uint8_t *b_cat, const int64_t *b_off,
+int paco_lcs_batch(paco_ctx *ctx, const uint8_t *a_cat, const uint8_t *b_cat,
                    const int64_t *h_a_off, const int64_t *h_b_off, int32_t npairs,
-                   int32_t *d_len, int32_t *d_rows_cat, const int64_t *row_off,
-                   int32_t *d_cols_cat, const int64_t *col_off, void *stream);
+                   int32_t *d_len, int32_t *d_rows_cat, const int64_t *h_row_off,
+                   int32_t *d_cols_cat, const int64_t *h_col_off, void *stream);
 
 /* ---- serving: continuous batching ------------------------------------- */
 

@@ -81,7 +81,7 @@ def load():
         "paco_lcs_length": ([P, P, I64, P, I64, P, P], INT),
         "paco_lcs_boundaries": ([P, P, I64, P, I64, P, P, P, P, P, P], INT),
         "paco_lcs_boundaries_host": ([P, P, I64, P, I64, P, P, P, P, P, P], INT),
-        "paco_lcs_batch": ([P, P, P, P, P, P, P, I32, P, P, P, P, P, P], INT),
+        "paco_lcs_batch": ([P, P, P, P, P, I32, P, P, P, P, P, P], INT),
         "paco_lcs_submit": ([P, P, I64, P, I64, INT, ctypes.POINTER(ctypes.c_uint64)], INT),
         "paco_lcs_poll": ([P, ctypes.c_uint64, P, P, P], INT),
         "paco_serve_get_stats": ([P, ctypes.POINTER(PacoServeStats)], INT),
@@ -232,21 +232,23 @@ def paco_lcs_boundaries_host_ptr(ctx: Context, a_ptr, n, b_ptr, m, row_ptr, col_
                                            len_ptr, None), ctx)
 
 
-def paco_lcs_batch(ctx: Context, a_cat, a_off, b_cat, b_off, h_a_off, h_b_off, lengths=None,
-                   rows_cat=None, row_off=None, cols_cat=None, col_off=None, stream=None):
-    """Batch of independent pairs: device concatenations + int64 offsets
-    (device and host copies).  Returns the int32[npairs] length tensor."""
+def paco_lcs_batch(ctx: Context, a_cat, b_cat, h_a_off, h_b_off, lengths=None, rows_cat=None,
+                   h_row_off=None, cols_cat=None, h_col_off=None, stream=None):
+    """Batch of independent pairs: device concatenations (uint8 tensors) and
+    HOST int64 offsets.  Returns the int32[npairs] length tensor; optional
+    device outputs rows_cat/cols_cat at the host offsets h_row_off/h_col_off."""
     import numpy as np
     import torch
-    npairs = len(h_a_off) - 1
     h_a_off = np.ascontiguousarray(h_a_off, dtype=np.int64)
     h_b_off = np.ascontiguousarray(h_b_off, dtype=np.int64)
+    npairs = h_a_off.size - 1
     if lengths is None:
         lengths = torch.empty(max(npairs, 1), dtype=torch.int32, device=a_cat.device)
-    _check(load().paco_lcs_batch(ctx.handle, _ptr(a_cat), _ptr(a_off), _ptr(b_cat), _ptr(b_off),
-                                 h_a_off.ctypes.data_as(ctypes.c_void_p),
-                                 h_b_off.ctypes.data_as(ctypes.c_void_p), npairs, _ptr(lengths),
-                                 _ptr(rows_cat), _ptr(row_off), _ptr(cols_cat), _ptr(col_off),
+    ro = None if h_row_off is None else np.ascontiguousarray(h_row_off, dtype=np.int64)
+    co = None if h_col_off is None else np.ascontiguousarray(h_col_off, dtype=np.int64)
+    p = lambda x: None if x is None else x.ctypes.data_as(ctypes.c_void_p)
+    _check(load().paco_lcs_batch(ctx.handle, _ptr(a_cat), _ptr(b_cat), p(h_a_off), p(h_b_off), npairs,
+                                 _ptr(lengths), _ptr(rows_cat), p(ro), _ptr(cols_cat), p(co),
                                  _stream(stream)), ctx)
     return lengths
 

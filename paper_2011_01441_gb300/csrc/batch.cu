@@ -1,18 +1,677 @@
-// Batch of independent pairs (placeholder until the batch engine lands).
+// Batch of independent pairs in one persistent launch (CUDA-graph captured).
+//
+// Every pair is a table of Eq. (1) (Tang & Gao, Sec. "PACO LCS") with zero
+// first row/column.  Its rows run along the bits of the longer string; the
+// rows are cut into segments of at most 32 lanes x 31 rows, each segment is
+// one warp job that streams all columns of the pair; a pair taller than one
+// warp chains its segments through epoch-tagged carry words in global memory
+// (the same hand-off the single-pair strips use).  Jobs are ordered largest
+// pair first (LPT), so the persistent warps, which take jobs from one atomic
+// ticket, end together: this is the balanced share of cells per SM the PACO
+// partition asks for, here over independent pairs instead of one table.
 #include "../../include/paco_lcs.h"
+#include "bp_device.cuh"
 #include "ctx.hpp"
+#include "paco_internal.hpp"
+
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <numeric>
+#include <vector>
 
 namespace paco {
-struct BatchState {};
+
+namespace {
+
+using namespace dev;
+
+enum : uint32_t { kTransposed = 1u, kInGlobal = 2u, kOutGlobal = 4u, kFinal = 8u };
+
+struct SegJob {
+    int64_t rows_off;  // first row of the segment in the rows string (cat offset)
+    int64_t cols_off;  // first column of the pair in the column string (cat offset)
+    int32_t nrows;     // rows of this segment (1 .. 992)
+    int32_t S;         // columns of the pair
+    int32_t pair;
+    uint32_t flags;
+    int64_t hin;       // tagged input carry row (kInGlobal)
+    int64_t hout;      // tagged output carry row (kOutGlobal)
+    int64_t rword;     // first right-column lane word of the segment, or -1
+    int64_t bword;     // first bottom-row step word of the pair (kFinal), or -1
+};
+// (cols_off indexes the column-offset array, not the concatenation)
+
+// One pair's streamed string -> its column-table offsets at a 16-byte
+// aligned position of the batch's offset array.
+struct ColJob {
+    int64_t src;      // offset of the streamed string in its concatenation
+    int64_t dst;      // offset in the column-offset array (multiple of 4)
+    int64_t len;
+    int32_t from_a;   // 1: the streamed string is in a_cat
+    int32_t pad;
+};
+
+__global__ void k_pair_column_offsets(const uint8_t *a_cat, const uint8_t *b_cat, const ColJob *cj,
+                                      uint32_t *coffs) {
+    const ColJob J = cj[blockIdx.x];
+    const uint8_t *src = (J.from_a ? a_cat : b_cat) + J.src;
+    for (int64_t j = threadIdx.x; j < J.len; j += blockDim.x) coffs[J.dst + j] = (uint32_t)src[j] * 128u;
+}
+
+struct BatchArgs {
+    const uint8_t *a_cat, *b_cat;
+    const uint32_t *coffs;  // column-table offsets, pair by pair (16-byte aligned starts)
+    const SegJob *jobs;
+    int64_t njobs;
+    uint64_t *hbuf;
+    uint32_t *rbits;
+    uint32_t *bbits;
+    int32_t *len;
+    int *ticket;
+    int *err;
+    const uint32_t *epoch_dev;
+    long long wait_limit_ns;
+};
+
+constexpr int kBatchSrcRing = 8;
+constexpr int kBatchSrcAhead = 4;
+
+template <int C>
+__global__ void __launch_bounds__(32) k_batch(const BatchArgs P) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ __align__(16) uint64_t s_src[2 * kBatchSrcRing];
+    const int lane = threadIdx.x & 31;
+    uint32_t *pm = reinterpret_cast<uint32_t *>(smem);
+    const uint32_t pm_lane = (uint32_t)__cvta_generic_to_shared(pm + lane);
+    const uint32_t src_ring = (uint32_t)__cvta_generic_to_shared(s_src);
+    for (int c = 0; c < kMaxSigma; ++c) pm[c * 32 + lane] = 0u;
+    const uint32_t epoch = *P.epoch_dev;
+
+    constexpr int K = 32 / C;
+    constexpr uint32_t cmask = (C == 32) ? kFull : ((1u << C) - 1u);
+    constexpr int kFlushStep = 30 % K;  // lane 31 trails lane 0 by 31 chunks
+
+    for (;;) {
+        int job = 0;
+        if (lane == 0) {
+            job = atomicAdd(P.ticket, 1);
+            if (ld_relaxed_i32(P.err) != 0) job = (int)P.njobs;
+        }
+        job = __shfl_sync(kFull, job, 0);
+        if (job >= P.njobs) break;
+        const SegJob J = P.jobs[job];
+        const bool tr = (J.flags & kTransposed) != 0;
+        const uint8_t *rows = tr ? P.b_cat : P.a_cat;
+        const uint32_t *boff = P.coffs + J.cols_off;
+        const int64_t S = J.S;
+        const int64_t rbase = J.rows_off + (int64_t)lane * kLaneRows;
+        const int left_rows = J.nrows - lane * kLaneRows;
+        const int nreal = left_rows <= 0 ? 0 : (left_rows >= kLaneRows ? kLaneRows : left_rows);
+        const uint32_t realmask = (1u << nreal) - 1u;
+        uint32_t aw[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) aw[k] = 0;
+#pragma unroll
+        for (int r = 0; r < kLaneRows; ++r)
+            if (r < nreal) aw[r >> 2] |= (uint32_t)__ldg(rows + rbase + r) << ((r & 3) * 8);
+#pragma unroll
+        for (int r = 0; r < kLaneRows; ++r) {
+            if (r < nreal) {
+                const uint32_t ch = (aw[r >> 2] >> ((r & 3) * 8)) & 0xffu;
+                pm[ch * 32 + lane] |= 1u << r;
+            }
+        }
+        uint32_t Sv = kK31, Yv = 0;  // zero first column: no vertical steps
+        __syncwarp();
+
+        const int64_t nch = (S + C - 1) / C;
+        const int last_valid = (int)(S - (nch - 1) * C);
+        const int64_t nwords = (S + 31) >> 5;
+        const int64_t npairs = (nwords + 1) >> 1;
+        const int64_t nouter = (nch + 31 + K - 1) / K;
+        const bool in_global = (J.flags & kInGlobal) != 0;
+        const uint64_t *src_row = P.hbuf + J.hin;
+        auto issue_pair = [&](int64_t pr) {
+            if (pr < npairs) {
+                const uint32_t dst = src_ring + (uint32_t)((pr % kBatchSrcRing) * 16);
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src_row + 2 * pr)
+                             : "memory");
+            }
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        };
+        if (in_global && lane == 0)
+            for (int d = 0; d < kBatchSrcAhead; ++d) issue_pair(d);
+
+        uint32_t cw_last = 0, gw = 0, total = 0;
+        uint32_t win[32], wnext[32];
+        bool ok = true;
+        load_window(boff, -(int64_t)lane * C, S, win);
+        for (int64_t u = 0; u < nouter; ++u) {
+            uint32_t srcw = 0;
+            bool lok = true;
+            if (lane == 0 && in_global && u < nwords) {
+                if ((u & 1) == 0) {
+                    asm volatile("cp.async.wait_group %0;" ::"n"(kBatchSrcAhead - 1) : "memory");
+                    issue_pair((u >> 1) + kBatchSrcAhead);
+                }
+                const uint32_t slot = src_ring + (uint32_t)((((u >> 1) % kBatchSrcRing) * 16) + (u & 1) * 8);
+                uint64_t v;
+                asm volatile("ld.shared.u64 %0, [%1];" : "=l"(v) : "r"(slot) : "memory");
+                if ((uint32_t)(v >> 32) != epoch) v = poll_global_lane(src_row + u, epoch, P.err, P.wait_limit_ns, lok);
+                srcw = (uint32_t)v;
+            }
+            if (!__all_sync(kFull, lok)) {
+                ok = false;
+                break;
+            }
+            const int64_t ubase = u * K;
+            const int64_t col0 = (ubase - lane) * C;
+            if (u + 1 < nouter) load_window(boff, col0 + 32, S, wnext);
+#pragma unroll
+            for (int i = 0; i < K; ++i) {
+                const int64_t q = ubase + i - lane;
+                const uint32_t up = __shfl_up_sync(kFull, cw_last, 1);
+                uint32_t sr = (lane == 0) ? (srcw << (i * C)) : (up << (32 - C));
+                uint32_t cw = 0;
+                const bool act = (q >= 0) && (q < nch);
+                if (act) {
+                    if (q == nch - 1 && last_valid < C) {
+#pragma unroll
+                        for (int jj = 0; jj < C; ++jj) {
+                            if (jj < last_valid) {
+                                const uint32_t M = lds_u32(pm_lane + win[i * C + jj]);
+                                column31(Sv, Yv, sr, cw, M);
+                            }
+                        }
+                        cw <<= (C - last_valid);
+                    } else {
+#pragma unroll
+                        for (int jj = 0; jj < C; ++jj) {
+                            const uint32_t M = lds_u32(pm_lane + win[i * C + jj]);
+                            column31(Sv, Yv, sr, cw, M);
+                        }
+                    }
+                }
+                cw_last = cw;
+                if (lane == 31 && act) {
+                    gw |= cw << (32 - C - ((q * C) & 31));
+                    if (i == kFlushStep || q == nch - 1) {
+                        const int64_t wq = (q * C) >> 5;
+                        if (J.flags & kOutGlobal) {
+                            st_relaxed_u64(P.hbuf + J.hout + wq, ((uint64_t)epoch << 32) | gw);
+                        } else {
+                            total += __popc(gw);
+                            if (J.bword >= 0) P.bbits[J.bword + wq] = gw;
+                        }
+                        gw = 0;
+                    }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 32; ++k) win[k] = wnext[k];
+        }
+        if (in_global && lane == 0) asm volatile("cp.async.wait_all;" ::: "memory");
+        if (ok && lane == 31 && (J.flags & kFinal)) P.len[J.pair] = (int32_t)total;
+        if (ok && J.rword >= 0 && nreal > 0) P.rbits[J.rword + lane] = ~(Sv | Yv) & realmask;
+#pragma unroll
+        for (int r = 0; r < kLaneRows; ++r) {
+            if (r < nreal) {
+                const uint32_t ch = (aw[r >> 2] >> ((r & 3) * 8)) & 0xffu;
+                pm[ch * 32 + lane] = 0u;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+__global__ void k_bump_epoch(uint32_t *e) {
+    uint32_t v = *e + 1;
+    if (v == 0) v = 1;
+    *e = v;
+}
+
+// Per-pair prefixes: bottom row from the final segment's step bits (MSB-first
+// words) and right column from the lane words (31 rows each), written with
+// the transposition undone.
+struct PrefixJob {
+    int64_t bword;    // bottom-row step words (or -1)
+    int64_t rword;    // right-column lane words (or -1)
+    int64_t L, S;     // kernel rows / columns
+    int64_t out_bottom;  // offset into rows_cat or cols_cat
+    int64_t out_right;
+    int32_t transposed;
+    int32_t pad;
+};
+
+__device__ void block_prefix(const uint32_t *words, int bpw, bool msb_first, int64_t nbits, int32_t *out) {
+    __shared__ int32_t warp_tot[32];
+    __shared__ int32_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    if (out == nullptr) return;
+    if (threadIdx.x == 0) out[0] = 0;
+    __syncthreads();
+    const int64_t nw = (nbits + bpw - 1) / bpw;
+    for (int64_t base = 0; base < nw; base += blockDim.x) {
+        const int64_t k = base + threadIdx.x;
+        uint32_t word = 0;
+        if (k < nw) {
+            word = words[k];
+            if (msb_first) word = __brev(word);
+            const int64_t rem = nbits - k * bpw;
+            if (rem < 32) word &= (1u << rem) - 1u;
+        }
+        const int32_t c = __popc(word);
+        int32_t inc = c;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(kFull, inc, o);
+            if ((threadIdx.x & 31) >= o) inc += y;
+        }
+        if ((threadIdx.x & 31) == 31) warp_tot[threadIdx.x >> 5] = inc;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            const int32_t t = threadIdx.x < (blockDim.x >> 5) ? warp_tot[threadIdx.x] : 0;
+            int32_t ti = t;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int32_t y = __shfl_up_sync(kFull, ti, o);
+                if (threadIdx.x >= o) ti += y;
+            }
+            warp_tot[threadIdx.x] = ti - t;
+        }
+        __syncthreads();
+        const int32_t before = carry + warp_tot[threadIdx.x >> 5] + inc - c;
+        if (k < nw) {
+            const int64_t e0 = k * bpw;
+            const int ne = (int)min((int64_t)bpw, nbits - e0);
+            int32_t run = before;
+            for (int b = 0; b < ne; ++b) {
+                run += (word >> b) & 1u;
+                out[e0 + b + 1] = run;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = before + c;
+        __syncthreads();
+    }
+}
+
+__global__ void k_batch_prefix(const PrefixJob *pj, const uint32_t *bbits, const uint32_t *rbits,
+                               int32_t *rows_cat, int32_t *cols_cat) {
+    const PrefixJob J = pj[blockIdx.x];
+    // kernel bottom row (S+1 values) and kernel right column (L+1 values)
+    int32_t *kb = J.transposed ? (cols_cat ? cols_cat + J.out_bottom : nullptr)
+                               : (rows_cat ? rows_cat + J.out_bottom : nullptr);
+    int32_t *kr = J.transposed ? (rows_cat ? rows_cat + J.out_right : nullptr)
+                               : (cols_cat ? cols_cat + J.out_right : nullptr);
+    if (J.bword >= 0) block_prefix(bbits + J.bword, 32, true, J.S, kb);
+    else if (kb) for (int64_t j = threadIdx.x; j <= J.S; j += blockDim.x) kb[j] = 0;
+    __syncthreads();
+    if (J.rword >= 0) block_prefix(rbits + J.rword, 31, false, J.L, kr);
+    else if (kr) for (int64_t i = threadIdx.x; i <= J.L; i += blockDim.x) kr[i] = 0;
+}
+
+template <int C>
+cudaError_t launch_batch_c(const BatchArgs &a, int grid, cudaStream_t st) {
+    const size_t smem = (size_t)kMaxSigma * 32 * 4;
+    cudaError_t e = cudaFuncSetAttribute(k_batch<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_batch<C><<<grid, 32, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int C>
+int batch_occupancy() {
+    const size_t smem = (size_t)kMaxSigma * 32 * 4;
+    if (cudaFuncSetAttribute(k_batch<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return 1;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<C>, 32, smem) != cudaSuccess) return 1;
+    return std::max(1, nb);
+}
+
+cudaError_t launch_batch(int C, const BatchArgs &a, int grid, cudaStream_t st) {
+    switch (C) {
+        case 2: return launch_batch_c<2>(a, grid, st);
+        case 4: return launch_batch_c<4>(a, grid, st);
+        case 8: return launch_batch_c<8>(a, grid, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+int occupancy_for(int C) {
+    switch (C) {
+        case 2: return batch_occupancy<2>();
+        case 4: return batch_occupancy<4>();
+        default: return batch_occupancy<8>();
+    }
+}
+
+struct Layout {
+    std::vector<SegJob> jobs;
+    std::vector<PrefixJob> pjobs;
+    std::vector<ColJob> cjobs;
+    int64_t cwords = 0;
+    int64_t hwords = 0, rwords = 0, bwords = 0;
+    int64_t cells = 0;
+};
+
+// Segments, carry rows and output word offsets for a batch; jobs in LPT
+// order (largest L*S first), the segments of a pair consecutive.
+void plan_batch(int32_t npairs, const int64_t *a_off, const int64_t *b_off, bool want_rows,
+                bool want_cols, const int64_t *row_off, const int64_t *col_off, Layout &lay) {
+    lay = Layout();
+    std::vector<int32_t> order((size_t)npairs);
+    std::iota(order.begin(), order.end(), 0);
+    std::vector<int64_t> work((size_t)npairs);
+    for (int32_t k = 0; k < npairs; ++k)
+        work[(size_t)k] = (a_off[k + 1] - a_off[k]) * (b_off[k + 1] - b_off[k]);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int32_t x, int32_t y) { return work[(size_t)x] > work[(size_t)y]; });
+    const int64_t seg_rows = 32 * 31;
+    for (int32_t k : order) {
+        const int64_t n = a_off[k + 1] - a_off[k], m = b_off[k + 1] - b_off[k];
+        const bool tr = m > n;
+        const int64_t L = tr ? m : n, S = tr ? n : m;
+        PrefixJob pj{};
+        pj.L = L;
+        pj.S = S;
+        pj.transposed = tr ? 1 : 0;
+        pj.out_bottom = tr ? (col_off ? col_off[k] : 0) : (row_off ? row_off[k] : 0);
+        pj.out_right = tr ? (row_off ? row_off[k] : 0) : (col_off ? col_off[k] : 0);
+        pj.bword = -1;
+        pj.rword = -1;
+        const bool want_bottom = tr ? want_cols : want_rows;
+        const bool want_right = tr ? want_rows : want_cols;
+        lay.cells += L * S;
+        if (L == 0 || S == 0) {
+            if (want_rows || want_cols) lay.pjobs.push_back(pj);
+            continue;
+        }
+        const int64_t nwords = (S + 31) / 32, hstride = (nwords + 1) & ~(int64_t)1;
+        const int64_t nseg = (L + seg_rows - 1) / seg_rows;
+        if (want_bottom) {
+            pj.bword = lay.bwords;
+            lay.bwords += nwords;
+        }
+        if (want_right) {
+            pj.rword = lay.rwords;
+            lay.rwords += nseg * 32;
+        }
+        ColJob cj{};
+        cj.src = tr ? a_off[k] : b_off[k];
+        cj.dst = lay.cwords;
+        cj.len = S;
+        cj.from_a = tr ? 1 : 0;
+        lay.cjobs.push_back(cj);
+        lay.cwords += (S + 3) & ~(int64_t)3;
+        int64_t prev_out = -1;
+        for (int64_t j = 0; j < nseg; ++j) {
+            SegJob J{};
+            J.rows_off = (tr ? b_off[k] : a_off[k]) + j * seg_rows;
+            J.cols_off = cj.dst;
+            J.nrows = (int32_t)std::min(seg_rows, L - j * seg_rows);
+            J.S = (int32_t)S;
+            J.pair = k;
+            J.flags = tr ? kTransposed : 0u;
+            J.hin = 0;
+            J.hout = 0;
+            if (j > 0) {
+                J.flags |= kInGlobal;
+                J.hin = prev_out;
+            }
+            if (j + 1 < nseg) {
+                J.flags |= kOutGlobal;
+                J.hout = lay.hwords;
+                prev_out = lay.hwords;
+                lay.hwords += hstride;
+            } else {
+                J.flags |= kFinal;
+                J.bword = pj.bword;
+            }
+            J.rword = pj.rword >= 0 ? pj.rword + j * 32 : -1;
+            if (J.flags & kFinal) J.bword = pj.bword;
+            else J.bword = -1;
+            lay.jobs.push_back(J);
+        }
+        if (want_rows || want_cols) lay.pjobs.push_back(pj);
+    }
+}
+
+uint64_t fnv(const void *p, size_t n, uint64_t h = 1469598103934665603ull) {
+    const unsigned char *c = (const unsigned char *)p;
+    for (size_t i = 0; i < n; ++i) {
+        h ^= c[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+}  // namespace
+
+struct BatchState {
+    int *ticket_ptr = nullptr;  // device ticket and error word this state launches with
+    int *err_ptr = nullptr;
+    // device copies of the current layout
+    DevBuf jobs, pjobs, cjobs, hbuf, rbits, bbits, coffs, epoch;
+    uint64_t layout_key = 0;
+    int64_t njobs = 0, npjobs = 0, ncjobs = 0;
+    // captured graph of the whole batch step
+    cudaGraphExec_t exec = nullptr;
+    uint64_t exec_key = 0;
+    // autotuned chunk width per layout signature
+    std::map<uint64_t, int> tuned;
+};
+
 void batch_release(paco_ctx *ctx) {
-    delete ctx->batch;
+    batch_state_free(ctx->batch);
     ctx->batch = nullptr;
 }
+
+namespace {
+
+// Enqueue the whole batch step (no allocation, capturable).
+cudaError_t enqueue_batch(paco_ctx *ctx, BatchState *B, int C, const uint8_t *a_cat, int64_t a_len,
+                          const uint8_t *b_cat, int64_t b_len, int32_t npairs, int32_t *d_len,
+                          int32_t *rows_cat, int32_t *cols_cat, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(B->ticket_ptr, 0, sizeof(int), st);
+    if (e == cudaSuccess && npairs > 0) e = cudaMemsetAsync(d_len, 0, (size_t)npairs * 4, st);
+    if (e != cudaSuccess) return e;
+    (void)a_len;
+    (void)b_len;
+    k_bump_epoch<<<1, 1, 0, st>>>((uint32_t *)B->epoch.ptr);
+    if (B->ncjobs > 0)
+        k_pair_column_offsets<<<(unsigned)B->ncjobs, 256, 0, st>>>(a_cat, b_cat, (const ColJob *)B->cjobs.ptr,
+                                                                   (uint32_t *)B->coffs.ptr);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (B->njobs > 0) {
+        BatchArgs A;
+        A.a_cat = a_cat;
+        A.b_cat = b_cat;
+        A.coffs = (const uint32_t *)B->coffs.ptr;
+        A.jobs = (const SegJob *)B->jobs.ptr;
+        A.njobs = B->njobs;
+        A.hbuf = (uint64_t *)B->hbuf.ptr;
+        A.rbits = (uint32_t *)B->rbits.ptr;
+        A.bbits = (uint32_t *)B->bbits.ptr;
+        A.len = d_len;
+        A.ticket = B->ticket_ptr;
+        A.err = B->err_ptr;
+        A.epoch_dev = (const uint32_t *)B->epoch.ptr;
+        A.wait_limit_ns = ctx->wait_limit_ns;
+        const int grid = (int)std::min<int64_t>(B->njobs, (int64_t)ctx->sms * occupancy_for(C));
+        e = launch_batch(C, A, grid, st);
+        if (e != cudaSuccess) return e;
+    }
+    if (B->npjobs > 0 && (rows_cat || cols_cat)) {
+        k_batch_prefix<<<(unsigned)B->npjobs, 256, 0, st>>>((const PrefixJob *)B->pjobs.ptr,
+                                                            (const uint32_t *)B->bbits.ptr,
+                                                            (const uint32_t *)B->rbits.ptr, rows_cat, cols_cat);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+}  // namespace
+
+BatchState *batch_state_new(int *ticket, int *err) {
+    BatchState *B = new (std::nothrow) BatchState();
+    if (B) {
+        B->ticket_ptr = ticket;
+        B->err_ptr = err;
+    }
+    return B;
+}
+
+void batch_state_free(BatchState *B) {
+    if (!B) return;
+    if (B->exec) cudaGraphExecDestroy(B->exec);
+    for (DevBuf *b : {&B->jobs, &B->pjobs, &B->cjobs, &B->hbuf, &B->rbits, &B->bbits, &B->coffs, &B->epoch})
+        if (b->ptr) cudaFree(b->ptr);
+    delete B;
+}
+
+int run_batch(paco_ctx *ctx, BatchState *B, const uint8_t *a_cat, const int64_t *h_a_off, const uint8_t *b_cat,
+              const int64_t *h_b_off, int32_t npairs, int32_t *d_len, int32_t *rows_cat,
+              const int64_t *h_row_off, int32_t *cols_cat, const int64_t *h_col_off, cudaStream_t st,
+              bool use_graph, int force_chunk) {
+    if (!B) return PACO_ENOMEM;
+    int rc;
+    const int64_t a_len = h_a_off[npairs], b_len = h_b_off[npairs];
+    // layout: depends on lengths and on which outputs are wanted (and where)
+    uint64_t key = fnv(h_a_off, sizeof(int64_t) * (npairs + 1));
+    key = fnv(h_b_off, sizeof(int64_t) * (npairs + 1), key);
+    const int want = (rows_cat ? 1 : 0) | (cols_cat ? 2 : 0);
+    key = fnv(&want, sizeof(want), key);
+    if (rows_cat) key = fnv(h_row_off, sizeof(int64_t) * npairs, key);
+    if (cols_cat) key = fnv(h_col_off, sizeof(int64_t) * npairs, key);
+    if (key != B->layout_key) {
+        Layout lay;
+        plan_batch(npairs, h_a_off, h_b_off, rows_cat != nullptr, cols_cat != nullptr, h_row_off, h_col_off, lay);
+        if ((rc = ensure_bytes(ctx, B->jobs, lay.jobs.size() * sizeof(SegJob) + 64)) != PACO_OK) return rc;
+        if ((rc = ensure_bytes(ctx, B->pjobs, lay.pjobs.size() * sizeof(PrefixJob) + 64)) != PACO_OK) return rc;
+        if ((rc = ensure_bytes(ctx, B->cjobs, lay.cjobs.size() * sizeof(ColJob) + 64)) != PACO_OK) return rc;
+        if ((rc = ensure_bytes(ctx, B->coffs, (size_t)lay.cwords * 4 + 64)) != PACO_OK) return rc;
+        if ((rc = ensure_bytes(ctx, B->hbuf, (size_t)lay.hwords * 8 + 64)) != PACO_OK) return rc;
+        if ((rc = ensure_bytes(ctx, B->rbits, (size_t)lay.rwords * 4 + 64)) != PACO_OK) return rc;
+        if ((rc = ensure_bytes(ctx, B->bbits, (size_t)lay.bwords * 4 + 64)) != PACO_OK) return rc;
+        if ((rc = ensure_bytes(ctx, B->epoch, 64)) != PACO_OK) return rc;
+        cudaError_t e = cudaSuccess;
+        if (!lay.jobs.empty())
+            e = cudaMemcpy(B->jobs.ptr, lay.jobs.data(), lay.jobs.size() * sizeof(SegJob), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && !lay.pjobs.empty())
+            e = cudaMemcpy(B->pjobs.ptr, lay.pjobs.data(), lay.pjobs.size() * sizeof(PrefixJob),
+                           cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && !lay.cjobs.empty())
+            e = cudaMemcpy(B->cjobs.ptr, lay.cjobs.data(), lay.cjobs.size() * sizeof(ColJob), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return set_cuda_error(ctx, e, "upload batch layout");
+        B->ncjobs = (int64_t)lay.cjobs.size();
+        B->njobs = (int64_t)lay.jobs.size();
+        B->npjobs = (int64_t)lay.pjobs.size();
+        B->layout_key = key;
+        if (B->exec) {
+            cudaGraphExecDestroy(B->exec);
+            B->exec = nullptr;
+            B->exec_key = 0;
+        }
+    }
+
+    // chunk width: forced, tuned for this layout, or tuned now
+    int C = force_chunk;
+    if (C == 0 && B != ctx->batch) C = 4;
+    if (C == 0) {
+        auto it = B->tuned.find(key);
+        if (it != B->tuned.end()) {
+            C = it->second;
+        } else {
+            float best = 1e30f;
+            C = 4;
+            for (int cand : {2, 4, 8}) {
+                float ms_sum = 0.f;
+                for (int rep = 0; rep < 2; ++rep) {
+                    cudaEventRecord(ctx->ev0, st);
+                    cudaError_t e = enqueue_batch(ctx, B, cand, a_cat, a_len, b_cat, b_len, npairs, d_len,
+                                                  rows_cat, cols_cat, st);
+                    cudaEventRecord(ctx->ev1, st);
+                    if (e == cudaSuccess) e = cudaEventSynchronize(ctx->ev1);
+                    if (e != cudaSuccess) return set_cuda_error(ctx, e, "batch autotune");
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+                    if (rep == 1) ms_sum += ms;
+                }
+                if (ms_sum < best) {
+                    best = ms_sum;
+                    C = cand;
+                }
+            }
+            B->tuned[key] = C;
+        }
+    }
+    const uint64_t exec_key = fnv(&C, sizeof(C),
+                                  fnv(&a_cat, sizeof(a_cat),
+                                      fnv(&b_cat, sizeof(b_cat),
+                                          fnv(&d_len, sizeof(d_len),
+                                              fnv(&rows_cat, sizeof(rows_cat),
+                                                  fnv(&cols_cat, sizeof(cols_cat), key))))));
+    const bool timing = (B == ctx->batch);
+    if (timing) cudaEventRecord(ctx->ev0, st);
+    cudaError_t e = cudaSuccess;
+    if (use_graph) {
+        if (!B->exec || B->exec_key != exec_key) {
+            if (B->exec) {
+                cudaGraphExecDestroy(B->exec);
+                B->exec = nullptr;
+            }
+            cudaStream_t cap = nullptr;
+            e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+            cudaGraph_t g = nullptr;
+            if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                cudaError_t e2 = enqueue_batch(ctx, B, C, a_cat, a_len, b_cat, b_len, npairs, d_len, rows_cat,
+                                               cols_cat, cap);
+                e = cudaStreamEndCapture(cap, &g);
+                if (e2 != cudaSuccess) e = e2;
+            }
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&B->exec, g, 0);
+            if (g) cudaGraphDestroy(g);
+            if (cap) cudaStreamDestroy(cap);
+            if (e != cudaSuccess) return set_cuda_error(ctx, e, "capture batch graph");
+            B->exec_key = exec_key;
+        }
+        e = cudaGraphLaunch(B->exec, st);
+    } else {
+        e = enqueue_batch(ctx, B, C, a_cat, a_len, b_cat, b_len, npairs, d_len, rows_cat, cols_cat, st);
+    }
+    if (timing) {
+        cudaEventRecord(ctx->ev1, st);
+        ctx->timed = true;
+        ctx->timed_name = "batch graph (k_batch)";
+        ctx->last_batch_chunk = C;
+    }
+    return e == cudaSuccess ? PACO_OK : (e == cudaErrorMemoryAllocation ? PACO_ENOMEM : PACO_EDEVICE);
+}
+
 }  // namespace paco
 
-extern "C" int paco_lcs_batch(paco_ctx *ctx, const uint8_t *, const int64_t *, const uint8_t *,
-                              const int64_t *, const int64_t *, const int64_t *, int32_t, int32_t *,
-                              int32_t *, const int64_t *, int32_t *, const int64_t *, void *) {
-    if (!ctx) return PACO_EINVAL;
-    return PACO_EINVAL;
+extern "C" int paco_lcs_batch(paco_ctx *ctx, const uint8_t *a_cat, const uint8_t *b_cat,
+                              const int64_t *h_a_off, const int64_t *h_b_off, int32_t npairs,
+                              int32_t *d_len, int32_t *d_rows_cat, const int64_t *h_row_off,
+                              int32_t *d_cols_cat, const int64_t *h_col_off, void *stream) {
+    if (!ctx || npairs < 0 || !h_a_off || !h_b_off) return PACO_EINVAL;
+    if (npairs > 0 && !d_len) return PACO_EINVAL;
+    if ((d_rows_cat && !h_row_off) || (d_cols_cat && !h_col_off)) return PACO_EINVAL;
+    for (int32_t k = 0; k < npairs; ++k) {
+        const int64_t n = h_a_off[k + 1] - h_a_off[k], m = h_b_off[k + 1] - h_b_off[k];
+        if (n < 0 || m < 0 || n > 0x7fffffffLL || m > 0x7fffffffLL) return PACO_EINVAL;
+    }
+    if (h_a_off[npairs] > 0 && !a_cat) return PACO_EINVAL;
+    if (h_b_off[npairs] > 0 && !b_cat) return PACO_EINVAL;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    cudaSetDevice(ctx->device);
+    const int force = ctx->opt_chunk == 0 ? 0 : std::min(8, std::max(2, ctx->opt_chunk));
+    if (!ctx->batch) ctx->batch = paco::batch_state_new(ctx->ticket_ptr(), ctx->err_ptr());
+    return paco::run_batch(ctx, ctx->batch, a_cat, h_a_off, b_cat, h_b_off, npairs, d_len, d_rows_cat, h_row_off,
+                           d_cols_cat, h_col_off, (cudaStream_t)stream, true, force);
 }

@@ -45,6 +45,7 @@ struct paco_ctx {
     char last_error[256] = {0};
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     bool timed = false;
+    int last_batch_chunk = 0;
     const char *timed_name = "";
     cudaStream_t own_stream = nullptr;
     std::map<std::tuple<int64_t, int64_t, int, int, int, int>, std::unique_ptr<paco::CachedPairPlan>> plans;
@@ -65,6 +66,13 @@ int run_pair(paco_ctx *ctx, const uint8_t *a, int64_t n, const uint8_t *b, int64
              const int32_t *top, const int32_t *left, int32_t *bottom_row, int32_t *right_col,
              int32_t *len, cudaStream_t st);
 const CachedPairPlan *get_pair_plan(paco_ctx *ctx, int64_t n, int64_t m, int *rc);
+// Enqueue a batch (device strings, host offsets); ctx->mu must be held.
+BatchState *batch_state_new(int *ticket, int *err);
+void batch_state_free(BatchState *B);
+int run_batch(paco_ctx *ctx, BatchState *B, const uint8_t *a_cat, const int64_t *h_a_off, const uint8_t *b_cat,
+              const int64_t *h_b_off, int32_t npairs, int32_t *d_len, int32_t *rows_cat,
+              const int64_t *h_row_off, int32_t *cols_cat, const int64_t *h_col_off, cudaStream_t st,
+              bool use_graph, int force_chunk);
 void serve_shutdown(paco_ctx *ctx);
 void batch_release(paco_ctx *ctx);
 }  // namespace paco
