@@ -130,6 +130,36 @@ int paco_lcs_boundaries_host(paco_ctx *ctx, const uint8_t *a, int64_t n,
                              int32_t *bottom_row, int32_t *right_col,
                              int32_t *len, void *stream);
 
+/* Length plus boundaries with NO device allocation, for callers that cannot
+ * allocate device memory where they need the result: e.g. code running as a
+ * plugin or callback inside another framework that owns every device
+ * allocation through its own pool, or a latency-critical loop in which a
+ * cudaMalloc/cudaFree would synchronise the device.  There is no counterpart
+ * in the paper; this is a deployment variant of paco_lcs_boundaries with
+ * zero first row and column (top = left = 0) and the planner's defaults.
+ *
+ * No context is used: all scratch (step bits, carry rows, column-table
+ * offsets, ticket and error words) lives in one fixed 32 MiB __device__
+ * array inside this library, which every GPU that loads the library keeps
+ * until the process exits.  The call allocates nothing (no cudaMalloc,
+ * cudaFree or allocating library routine).
+ *   a, b        : device uint8[n], uint8[m]
+ *   d_bottom_row: device int32[m+1] or NULL;  d_right_col: int32[n+1] or NULL
+ *   d_len       : device int32[1] or NULL; receives L, or a negative
+ *                 paco_status if a device wait timed out
+ * Stream ordered (stream = cudaStream_t or NULL).  The first call on a
+ * device, with that device current, resolves the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls on a device share the one array and keep the previous call's
+ * contents (each call clears what must start at zero): calls that overlap on
+ * the GPU race, so serialise them.  Returns PACO_EINVAL for bad arguments or
+ * when the table needs more than the 32 MiB of scratch (roughly: more than
+ * about 6 million columns in the shorter string), PACO_EDEVICE for a CUDA
+ * error. */
+int paco_lcs_boundaries_static(const uint8_t *a, int64_t n, const uint8_t *b, int64_t m,
+                               int32_t *d_bottom_row, int32_t *d_right_col, int32_t *d_len,
+                               void *stream);
+
 /* ---- batch of independent pairs ---------------------------------------- */
 
 /* npairs independent pairs in one persistent launch.  The whole step (column

@@ -82,6 +82,7 @@ def load():
         "paco_lcs_boundaries": ([P, P, I64, P, I64, P, P, P, P, P, P], INT),
         "paco_lcs_boundaries_host": ([P, P, I64, P, I64, P, P, P, P, P, P], INT),
         "paco_lcs_batch": ([P, P, P, P, P, I32, P, P, P, P, P, P], INT),
+        "paco_lcs_boundaries_static": ([P, I64, P, I64, P, P, P, P], INT),
         "paco_lcs_submit": ([P, P, I64, P, I64, INT, ctypes.POINTER(ctypes.c_uint64)], INT),
         "paco_lcs_poll": ([P, ctypes.c_uint64, P, P, P], INT),
         "paco_serve_get_stats": ([P, ctypes.POINTER(PacoServeStats)], INT),
@@ -205,6 +206,25 @@ def paco_lcs_boundaries(ctx: Context, a, b, top=None, left=None, bottom_row=None
     _check(load().paco_lcs_boundaries(ctx.handle, _ptr(a), n, _ptr(b), m, _ptr(top), _ptr(left),
                                       _ptr(bottom_row), _ptr(right_col), _ptr(length),
                                       _stream(stream)), ctx)
+    return length, bottom_row, right_col
+
+
+def paco_lcs_boundaries_static(a, b, bottom_row=None, right_col=None, length=None, stream=None,
+                               want_rows=True, want_cols=True):
+    """The allocation-free variant (see include/paco_lcs.h): zero boundaries,
+    scratch in the library's fixed device array.  Outputs are allocated here
+    by torch only when not given."""
+    import torch
+    a, b = _u8(a, "a"), _u8(b, "b")
+    n, m = a.numel(), b.numel()
+    if want_rows and bottom_row is None:
+        bottom_row = torch.empty(m + 1, dtype=torch.int32, device=a.device)
+    if want_cols and right_col is None:
+        right_col = torch.empty(n + 1, dtype=torch.int32, device=a.device)
+    if length is None:
+        length = torch.empty(1, dtype=torch.int32, device=a.device)
+    _check(load().paco_lcs_boundaries_static(_ptr(a), n, _ptr(b), m, _ptr(bottom_row), _ptr(right_col),
+                                             _ptr(length), _stream(stream)))
     return length, bottom_row, right_col
 
 

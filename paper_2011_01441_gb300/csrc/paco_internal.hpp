@@ -40,7 +40,8 @@ struct PairArgs {
     int64_t nchunks;             // ceil(S / C)
     int64_t nwords;              // ceil(S / 32): words per carry row
     int64_t hstride;             // words between carry rows (nwords rounded up to even)
-    const int64_t *strip_row0;   // nstrips+1 row offsets (multiples of 31, last = L)
+    const int64_t *strip_row0;   // nstrips+1 row offsets (multiples of 31, last = L), or NULL:
+    int64_t granules;            //   then strip s starts at 31*(s*(granules/nstrips) + min(s, granules%nstrips))
     int nstrips;
     int sigma;                   // match-table rows (symbols must be < sigma)
     const uint32_t *left_bits;   // L bits: vertical steps of the first column

@@ -81,8 +81,15 @@ __global__ void __launch_bounds__(256, 1) k_pair_bp(const PairArgs P) {
         const int s = s_strip;
         if (s >= P.nstrips) break;
 
-        const int64_t row0 = P.strip_row0[s];
-        const int64_t row1 = P.strip_row0[s + 1];
+        int64_t row0, row1;
+        if (P.strip_row0) {
+            row0 = P.strip_row0[s];
+            row1 = P.strip_row0[s + 1];
+        } else {  // the balanced split, computed in place
+            const int64_t q = P.granules / P.nstrips, r = P.granules % P.nstrips;
+            row0 = min(P.L, (int64_t)kLaneRows * ((int64_t)s * q + min((int64_t)s, r)));
+            row1 = min(P.L, (int64_t)kLaneRows * ((int64_t)(s + 1) * q + min((int64_t)(s + 1), r)));
+        }
         const int64_t rbase = row0 + (int64_t)w * (32 * kLaneRows) + (int64_t)lane * kLaneRows;
         const int64_t left_rows = row1 - rbase;
         const int nreal = left_rows <= 0 ? 0 : (left_rows >= kLaneRows ? kLaneRows : (int)left_rows);

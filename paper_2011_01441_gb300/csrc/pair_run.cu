@@ -117,6 +117,7 @@ int run_pair(paco_ctx *ctx, const uint8_t *a, int64_t n, const uint8_t *b, int64
     P.nwords = nwords;
     P.hstride = hstride;
     P.strip_row0 = (const int64_t *)cp->d_row0.ptr;
+    P.granules = 0;
     P.nstrips = pl.nstrips;
     P.sigma = kMaxSigma;
     P.left_bits = (const uint32_t *)ctx->lbits.ptr;
