@@ -276,6 +276,7 @@ def run_batch_bench(args):
     P.load()
     ctx = P.Context(0)
     bt = W.batch_pairs()
+    ctx.set_option(P.OPT_ALPHABET, 4)  # the workload's symbols are 0..3
     da = torch.from_numpy(bt.a_cat).cuda()
     db = torch.from_numpy(bt.b_cat).cuda()
     L = torch.empty(bt.npairs, dtype=torch.int32, device="cuda")
@@ -313,7 +314,8 @@ def run_batch_bench(args):
             "warmup": args.warmup, "ms_per_step": sum(ms) / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": bt.name + " (seed 4)", "pairs": bt.npairs, "cells": cells,
-                       "engine": "batch graph, warp jobs", "l2": "flushed between timed steps"},
+                       "engine": "batch graph, warp jobs", "alphabet": 4, "chunk": P.paco_last_batch_chunk(ctx) if hasattr(P, "paco_last_batch_chunk") else None,
+                       "l2": "flushed between timed steps"},
             "plain_one_pair_per_launch": {"value": cells / plain_s / 1e9, "unit": "GCUPS",
                                           "seconds": plain_s},
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
@@ -335,6 +337,7 @@ def run_serve_bench(args):
     import paper_2011_01441_gb300 as P
     P.load()
     ctx = P.Context(0, mem_budget_bytes=8 << 30)
+    ctx.set_option(P.OPT_ALPHABET, 20)  # the serving mix uses symbols 0..19
     nreq = args.requests
     reqs = [W.serve_request(k) for k in range(nreq)]
     cells = np.array([r.a.size * r.b.size for r in reqs], dtype=np.float64)

@@ -93,11 +93,15 @@ int paco_ctx_get_option(paco_ctx *ctx, int option, int64_t *value);
 
 enum paco_option {
     PACO_OPT_ENGINE = 1,        /* 0 = auto, 1 = bit-parallel, 2 = cell-wise   */
-    PACO_OPT_CHUNK = 2,         /* columns per lane hand-off: 2,4,8,16,32 (0 = planner) */
+    PACO_OPT_CHUNK = 2,         /* columns per lane hand-off: 2, 4 or 8 (0 = planner) */
     PACO_OPT_WARPS = 3,         /* warps per CTA strip (0 = planner)           */
     PACO_OPT_WAIT_LIMIT_NS = 4, /* bounded-wait limit per wait, ns (default 2e9) */
     PACO_OPT_ORIENT = 5,        /* 0 = planner, 1 = bits along a, 2 = along b  */
     PACO_OPT_SCHEDULE = 6,      /* 0 = PACO balanced strips, 1 = uniform strips */
+    PACO_OPT_ALPHABET = 7,      /* batch and serving: symbols are < this (1..256, default
+                                   256); a smaller alphabet shrinks the per-warp match
+                                   table and raises occupancy.  A symbol outside it never
+                                   matches and the call reports PACO_EINVAL */
     PACO_OPT_TEST_STALL = 100   /* tests only: make one strip wait on a flag
                                    nothing sets (exercises the bounded wait) */
 };

@@ -142,8 +142,7 @@ int paco_ctx_set_option(paco_ctx *ctx, int option, int64_t value) {
             ctx->opt_engine = (int)value;
             return PACO_OK;
         case PACO_OPT_CHUNK:
-            if (!(value == 0 || value == 2 || value == 4 || value == 8 || value == 16 ||
-                  value == 32))
+            if (!(value == 0 || value == 2 || value == 4 || value == 8))
                 return PACO_EINVAL;
             ctx->opt_chunk = (int)value;
             return PACO_OK;
@@ -163,6 +162,10 @@ int paco_ctx_set_option(paco_ctx *ctx, int option, int64_t value) {
             if (value < 0 || value > 1) return PACO_EINVAL;
             ctx->opt_schedule = (int)value;
             return PACO_OK;
+        case PACO_OPT_ALPHABET:
+            if (value < 1 || value > 256) return PACO_EINVAL;
+            ctx->opt_alphabet = (int)value;
+            return PACO_OK;
         case PACO_OPT_TEST_STALL:
             if (value < -1 || value > 0x7fffffff) return PACO_EINVAL;
             ctx->test_stall = (int)value;
@@ -181,6 +184,7 @@ int paco_ctx_get_option(paco_ctx *ctx, int option, int64_t *value) {
         case PACO_OPT_WAIT_LIMIT_NS: *value = ctx->wait_limit_ns; return PACO_OK;
         case PACO_OPT_ORIENT: *value = ctx->opt_orient; return PACO_OK;
         case PACO_OPT_SCHEDULE: *value = ctx->opt_schedule; return PACO_OK;
+        case PACO_OPT_ALPHABET: *value = ctx->opt_alphabet; return PACO_OK;
         case PACO_OPT_TEST_STALL: *value = ctx->test_stall; return PACO_OK;
         default: return PACO_EINVAL;
     }

@@ -54,11 +54,22 @@ struct ColJob {
     int32_t pad;
 };
 
+// Symbols outside the declared alphabet (>= sigma) point at the table's
+// spare all-zero row and raise PACO_EINVAL.
 __global__ void k_pair_column_offsets(const uint8_t *a_cat, const uint8_t *b_cat, const ColJob *cj,
-                                      uint32_t *coffs) {
+                                      uint32_t *coffs, int sigma, int *err) {
     const ColJob J = cj[blockIdx.x];
     const uint8_t *src = (J.from_a ? a_cat : b_cat) + J.src;
-    for (int64_t j = threadIdx.x; j < J.len; j += blockDim.x) coffs[J.dst + j] = (uint32_t)src[j] * 128u;
+    bool bad = false;
+    for (int64_t j = threadIdx.x; j < J.len; j += blockDim.x) {
+        uint32_t c = src[j];
+        if ((int)c >= sigma) {
+            bad = true;
+            c = (uint32_t)sigma;
+        }
+        coffs[J.dst + j] = c * 128u;
+    }
+    if (bad) atomicCAS(err, 0, kEinval);
 }
 
 struct BatchArgs {
@@ -74,20 +85,28 @@ struct BatchArgs {
     int *err;
     const uint32_t *epoch_dev;
     long long wait_limit_ns;
+    int sigma;       // declared alphabet: symbols are < sigma
+    int table_rows;  // rows of the per-warp match table (sigma, plus a zero row when < 256)
 };
 
 constexpr int kBatchSrcRing = 8;
 constexpr int kBatchSrcAhead = 4;
+// column offsets through a shared ring of 32-column words, copied kColAhead
+// words ahead (lane 31 trails lane 0 by at most 31*8/32 + 1 = 9 words)
+constexpr int kColRing = 32;
+constexpr int kColAhead = 8;
 
 template <int C>
 __global__ void __launch_bounds__(32) k_batch(const BatchArgs P) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ __align__(16) uint64_t s_src[2 * kBatchSrcRing];
+    __shared__ __align__(16) uint32_t s_cols[kColRing * 32];
     const int lane = threadIdx.x & 31;
     uint32_t *pm = reinterpret_cast<uint32_t *>(smem);
     const uint32_t pm_lane = (uint32_t)__cvta_generic_to_shared(pm + lane);
+    const uint32_t col_ring = (uint32_t)__cvta_generic_to_shared(s_cols);
     const uint32_t src_ring = (uint32_t)__cvta_generic_to_shared(s_src);
-    for (int c = 0; c < kMaxSigma; ++c) pm[c * 32 + lane] = 0u;
+    for (int c = 0; c < P.table_rows; ++c) pm[c * 32 + lane] = 0u;
     const uint32_t epoch = *P.epoch_dev;
 
     constexpr int K = 32 / C;
@@ -117,13 +136,16 @@ __global__ void __launch_bounds__(32) k_batch(const BatchArgs P) {
 #pragma unroll
         for (int r = 0; r < kLaneRows; ++r)
             if (r < nreal) aw[r >> 2] |= (uint32_t)__ldg(rows + rbase + r) << ((r & 3) * 8);
+        bool badsym = false;
 #pragma unroll
         for (int r = 0; r < kLaneRows; ++r) {
             if (r < nreal) {
                 const uint32_t ch = (aw[r >> 2] >> ((r & 3) * 8)) & 0xffu;
-                pm[ch * 32 + lane] |= 1u << r;
+                if ((int)ch < P.sigma) pm[ch * 32 + lane] |= 1u << r;
+                else badsym = true;
             }
         }
+        if (badsym) atomicCAS(P.err, 0, kEinval);
         uint32_t Sv = kK31, Yv = 0;  // zero first column: no vertical steps
         __syncwarp();
 
@@ -146,10 +168,46 @@ __global__ void __launch_bounds__(32) k_batch(const BatchArgs P) {
             for (int d = 0; d < kBatchSrcAhead; ++d) issue_pair(d);
 
         uint32_t cw_last = 0, gw = 0, total = 0;
-        uint32_t win[32], wnext[32];
         bool ok = true;
-        load_window(boff, -(int64_t)lane * C, S, win);
+        auto issue_cols = [&](int64_t wd) {
+            if (lane < 8 && wd < nwords) {
+                const int64_t col = wd * 32 + lane * 4;
+                const int64_t rem = S - col;
+                const int bytes = rem >= 4 ? 16 : (rem > 0 ? (int)rem * 4 : 0);
+                const uint32_t *src = boff + (bytes > 0 ? col : 0);
+                const uint32_t dst = col_ring + (uint32_t)(((wd % kColRing) * 32 + lane * 4) * 4);
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes)
+                             : "memory");
+            }
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        };
+        auto offs_of = [&](int64_t q, uint32_t (&o)[C]) {
+            const int64_t col = q * C;
+            const uint32_t addr = col_ring + (uint32_t)(((((col >> 5) % kColRing) + kColRing) % kColRing) * 128 +
+                                                        (col & 31) * 4);
+            if constexpr (C == 2) {
+                uint32_t x, y;
+                asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(x), "=r"(y) : "r"(addr));
+                o[0] = x;
+                o[1] = y;
+            } else {
+#pragma unroll
+                for (int k = 0; k < C / 4; ++k) {
+                    uint32_t x, y, z, v;
+                    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                                 : "=r"(x), "=r"(y), "=r"(z), "=r"(v) : "r"(addr + 16 * k));
+                    o[4 * k] = x;
+                    o[4 * k + 1] = y;
+                    o[4 * k + 2] = z;
+                    o[4 * k + 3] = v;
+                }
+            }
+        };
+        for (int d = 0; d < kColAhead; ++d) issue_cols(d);
         for (int64_t u = 0; u < nouter; ++u) {
+            asm volatile("cp.async.wait_group %0;" ::"n"(kColAhead - 1) : "memory");
+            __syncwarp();
+            issue_cols(u + kColAhead);
             uint32_t srcw = 0;
             bool lok = true;
             if (lane == 0 && in_global && u < nwords) {
@@ -168,11 +226,12 @@ __global__ void __launch_bounds__(32) k_batch(const BatchArgs P) {
                 break;
             }
             const int64_t ubase = u * K;
-            const int64_t col0 = (ubase - lane) * C;
-            if (u + 1 < nouter) load_window(boff, col0 + 32, S, wnext);
+            uint32_t ocur[C], onext[C];
+            offs_of(ubase - lane, ocur);
 #pragma unroll
             for (int i = 0; i < K; ++i) {
                 const int64_t q = ubase + i - lane;
+                if (i + 1 < K) offs_of(q + 1, onext);
                 const uint32_t up = __shfl_up_sync(kFull, cw_last, 1);
                 uint32_t sr = (lane == 0) ? (srcw << (i * C)) : (up << (32 - C));
                 uint32_t cw = 0;
@@ -182,7 +241,7 @@ __global__ void __launch_bounds__(32) k_batch(const BatchArgs P) {
 #pragma unroll
                         for (int jj = 0; jj < C; ++jj) {
                             if (jj < last_valid) {
-                                const uint32_t M = lds_u32(pm_lane + win[i * C + jj]);
+                                const uint32_t M = lds_u32(pm_lane + ocur[jj]);
                                 column31(Sv, Yv, sr, cw, M);
                             }
                         }
@@ -190,11 +249,13 @@ __global__ void __launch_bounds__(32) k_batch(const BatchArgs P) {
                     } else {
 #pragma unroll
                         for (int jj = 0; jj < C; ++jj) {
-                            const uint32_t M = lds_u32(pm_lane + win[i * C + jj]);
+                            const uint32_t M = lds_u32(pm_lane + ocur[jj]);
                             column31(Sv, Yv, sr, cw, M);
                         }
                     }
                 }
+#pragma unroll
+                for (int jj = 0; jj < C; ++jj) ocur[jj] = onext[jj];
                 cw_last = cw;
                 if (lane == 31 && act) {
                     gw |= cw << (32 - C - ((q * C) & 31));
@@ -210,17 +271,17 @@ __global__ void __launch_bounds__(32) k_batch(const BatchArgs P) {
                     }
                 }
             }
-#pragma unroll
-            for (int k = 0; k < 32; ++k) win[k] = wnext[k];
         }
-        if (in_global && lane == 0) asm volatile("cp.async.wait_all;" ::: "memory");
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        __syncwarp();
+
         if (ok && lane == 31 && (J.flags & kFinal)) P.len[J.pair] = (int32_t)total;
         if (ok && J.rword >= 0 && nreal > 0) P.rbits[J.rword + lane] = ~(Sv | Yv) & realmask;
 #pragma unroll
         for (int r = 0; r < kLaneRows; ++r) {
             if (r < nreal) {
                 const uint32_t ch = (aw[r >> 2] >> ((r & 3) * 8)) & 0xffu;
-                pm[ch * 32 + lane] = 0u;
+                if ((int)ch < P.sigma) pm[ch * 32 + lane] = 0u;
             }
         }
         __syncwarp();
@@ -314,17 +375,19 @@ __global__ void k_batch_prefix(const PrefixJob *pj, const uint32_t *bbits, const
 
 template <int C>
 cudaError_t launch_batch_c(const BatchArgs &a, int grid, cudaStream_t st) {
-    const size_t smem = (size_t)kMaxSigma * 32 * 4;
-    cudaError_t e = cudaFuncSetAttribute(k_batch<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = (size_t)a.table_rows * 32 * 4;
+    cudaError_t e = cudaFuncSetAttribute(k_batch<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(kMaxSigma * 32 * 4));
     if (e != cudaSuccess) return e;
     k_batch<C><<<grid, 32, smem, st>>>(a);
     return cudaGetLastError();
 }
 
 template <int C>
-int batch_occupancy() {
-    const size_t smem = (size_t)kMaxSigma * 32 * 4;
-    if (cudaFuncSetAttribute(k_batch<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+int batch_occupancy(int table_rows) {
+    const size_t smem = (size_t)table_rows * 32 * 4;
+    if (cudaFuncSetAttribute(k_batch<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kMaxSigma * 32 * 4)) !=
+        cudaSuccess)
         return 1;
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<C>, 32, smem) != cudaSuccess) return 1;
@@ -340,13 +403,15 @@ cudaError_t launch_batch(int C, const BatchArgs &a, int grid, cudaStream_t st) {
     }
 }
 
-int occupancy_for(int C) {
+int occupancy_for(int C, int table_rows) {
     switch (C) {
-        case 2: return batch_occupancy<2>();
-        case 4: return batch_occupancy<4>();
-        default: return batch_occupancy<8>();
+        case 2: return batch_occupancy<2>(table_rows);
+        case 4: return batch_occupancy<4>(table_rows);
+        default: return batch_occupancy<8>(table_rows);
     }
 }
+
+int table_rows_for(int sigma) { return sigma >= kMaxSigma ? kMaxSigma : sigma + 1; }
 
 struct Layout {
     std::vector<SegJob> jobs;
@@ -472,7 +537,7 @@ void batch_release(paco_ctx *ctx) {
 namespace {
 
 // Enqueue the whole batch step (no allocation, capturable).
-cudaError_t enqueue_batch(paco_ctx *ctx, BatchState *B, int C, const uint8_t *a_cat, int64_t a_len,
+cudaError_t enqueue_batch(paco_ctx *ctx, BatchState *B, int C, int sigma, const uint8_t *a_cat, int64_t a_len,
                           const uint8_t *b_cat, int64_t b_len, int32_t npairs, int32_t *d_len,
                           int32_t *rows_cat, int32_t *cols_cat, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(B->ticket_ptr, 0, sizeof(int), st);
@@ -483,7 +548,7 @@ cudaError_t enqueue_batch(paco_ctx *ctx, BatchState *B, int C, const uint8_t *a_
     k_bump_epoch<<<1, 1, 0, st>>>((uint32_t *)B->epoch.ptr);
     if (B->ncjobs > 0)
         k_pair_column_offsets<<<(unsigned)B->ncjobs, 256, 0, st>>>(a_cat, b_cat, (const ColJob *)B->cjobs.ptr,
-                                                                   (uint32_t *)B->coffs.ptr);
+                                                                   (uint32_t *)B->coffs.ptr, sigma, B->err_ptr);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (B->njobs > 0) {
@@ -501,7 +566,9 @@ cudaError_t enqueue_batch(paco_ctx *ctx, BatchState *B, int C, const uint8_t *a_
         A.err = B->err_ptr;
         A.epoch_dev = (const uint32_t *)B->epoch.ptr;
         A.wait_limit_ns = ctx->wait_limit_ns;
-        const int grid = (int)std::min<int64_t>(B->njobs, (int64_t)ctx->sms * occupancy_for(C));
+        A.sigma = sigma;
+        A.table_rows = table_rows_for(sigma);
+        const int grid = (int)std::min<int64_t>(B->njobs, (int64_t)ctx->sms * occupancy_for(C, A.table_rows));
         e = launch_batch(C, A, grid, st);
         if (e != cudaSuccess) return e;
     }
@@ -536,12 +603,14 @@ void batch_state_free(BatchState *B) {
 int run_batch(paco_ctx *ctx, BatchState *B, const uint8_t *a_cat, const int64_t *h_a_off, const uint8_t *b_cat,
               const int64_t *h_b_off, int32_t npairs, int32_t *d_len, int32_t *rows_cat,
               const int64_t *h_row_off, int32_t *cols_cat, const int64_t *h_col_off, cudaStream_t st,
-              bool use_graph, int force_chunk) {
+              bool use_graph, int force_chunk, int sigma) {
     if (!B) return PACO_ENOMEM;
+    if (sigma < 1 || sigma > kMaxSigma) sigma = kMaxSigma;
     int rc;
     const int64_t a_len = h_a_off[npairs], b_len = h_b_off[npairs];
     // layout: depends on lengths and on which outputs are wanted (and where)
     uint64_t key = fnv(h_a_off, sizeof(int64_t) * (npairs + 1));
+    key = fnv(&sigma, sizeof(sigma), key);
     key = fnv(h_b_off, sizeof(int64_t) * (npairs + 1), key);
     const int want = (rows_cat ? 1 : 0) | (cols_cat ? 2 : 0);
     key = fnv(&want, sizeof(want), key);
@@ -592,7 +661,7 @@ int run_batch(paco_ctx *ctx, BatchState *B, const uint8_t *a_cat, const int64_t 
                 float ms_sum = 0.f;
                 for (int rep = 0; rep < 2; ++rep) {
                     cudaEventRecord(ctx->ev0, st);
-                    cudaError_t e = enqueue_batch(ctx, B, cand, a_cat, a_len, b_cat, b_len, npairs, d_len,
+                    cudaError_t e = enqueue_batch(ctx, B, cand, sigma, a_cat, a_len, b_cat, b_len, npairs, d_len,
                                                   rows_cat, cols_cat, st);
                     cudaEventRecord(ctx->ev1, st);
                     if (e == cudaSuccess) e = cudaEventSynchronize(ctx->ev1);
@@ -629,7 +698,7 @@ int run_batch(paco_ctx *ctx, BatchState *B, const uint8_t *a_cat, const int64_t 
             cudaGraph_t g = nullptr;
             if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
             if (e == cudaSuccess) {
-                cudaError_t e2 = enqueue_batch(ctx, B, C, a_cat, a_len, b_cat, b_len, npairs, d_len, rows_cat,
+                cudaError_t e2 = enqueue_batch(ctx, B, C, sigma, a_cat, a_len, b_cat, b_len, npairs, d_len, rows_cat,
                                                cols_cat, cap);
                 e = cudaStreamEndCapture(cap, &g);
                 if (e2 != cudaSuccess) e = e2;
@@ -642,7 +711,7 @@ int run_batch(paco_ctx *ctx, BatchState *B, const uint8_t *a_cat, const int64_t 
         }
         e = cudaGraphLaunch(B->exec, st);
     } else {
-        e = enqueue_batch(ctx, B, C, a_cat, a_len, b_cat, b_len, npairs, d_len, rows_cat, cols_cat, st);
+        e = enqueue_batch(ctx, B, C, sigma, a_cat, a_len, b_cat, b_len, npairs, d_len, rows_cat, cols_cat, st);
     }
     if (timing) {
         cudaEventRecord(ctx->ev1, st);
@@ -673,5 +742,5 @@ extern "C" int paco_lcs_batch(paco_ctx *ctx, const uint8_t *a_cat, const uint8_t
     const int force = ctx->opt_chunk == 0 ? 0 : std::min(8, std::max(2, ctx->opt_chunk));
     if (!ctx->batch) ctx->batch = paco::batch_state_new(ctx->ticket_ptr(), ctx->err_ptr());
     return paco::run_batch(ctx, ctx->batch, a_cat, h_a_off, b_cat, h_b_off, npairs, d_len, d_rows_cat, h_row_off,
-                           d_cols_cat, h_col_off, (cudaStream_t)stream, true, force);
+                           d_cols_cat, h_col_off, (cudaStream_t)stream, true, force, ctx->opt_alphabet);
 }

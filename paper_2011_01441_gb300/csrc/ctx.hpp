@@ -41,6 +41,7 @@ struct paco_ctx {
     uint32_t epoch = 0;
     int opt_engine = 0, opt_chunk = 0, opt_warps = 0, opt_orient = 0, opt_schedule = 0;
     int test_stall = -1;
+    int opt_alphabet = 256;
     long long wait_limit_ns = 2000000000LL;
     char last_error[256] = {0};
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -72,7 +73,7 @@ void batch_state_free(BatchState *B);
 int run_batch(paco_ctx *ctx, BatchState *B, const uint8_t *a_cat, const int64_t *h_a_off, const uint8_t *b_cat,
               const int64_t *h_b_off, int32_t npairs, int32_t *d_len, int32_t *rows_cat,
               const int64_t *h_row_off, int32_t *cols_cat, const int64_t *h_col_off, cudaStream_t st,
-              bool use_graph, int force_chunk);
+              bool use_graph, int force_chunk, int sigma);
 void serve_shutdown(paco_ctx *ctx);
 void batch_release(paco_ctx *ctx);
 }  // namespace paco

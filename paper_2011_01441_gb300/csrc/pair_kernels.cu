@@ -36,22 +36,30 @@ constexpr int kSkew = 2;
 // Input-word ring of warp 0 (pairs of tagged words) and its prefetch depth.
 constexpr int kSrcRing = 8;
 constexpr int kSrcAhead = 4;
+// Column offsets reach each warp through a shared ring of kColRing 32-column
+// words, copied by cp.async kColAhead words ahead of lane 0 (the oldest word
+// still read, by lane 31, is at most 2*31*8/32 + 1 = 17 words behind).
+constexpr int kColRing = 32;
+constexpr int kColAhead = 8;
 
 template <int C>
 __global__ void __launch_bounds__(256, 1) k_pair_bp(const PairArgs P) {
+    static_assert(C == 2 || C == 4 || C == 8, "the column ring covers lane lags up to 17 words");
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_strip;
     const int W = blockDim.x >> 5;
     const int w = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     uint32_t *pm = reinterpret_cast<uint32_t *>(smem + (size_t)w * kTableBytes);
-    uint64_t *rings = reinterpret_cast<uint64_t *>(smem + (size_t)W * kTableBytes);
+    uint32_t *colring = reinterpret_cast<uint32_t *>(smem + (size_t)W * kTableBytes) + (size_t)w * kColRing * 32;
+    uint64_t *rings = reinterpret_cast<uint64_t *>(smem + (size_t)W * kTableBytes + (size_t)W * kColRing * 128);
     uint64_t *ring_out = rings + (size_t)w * kRing;                       // read by warp w+1
     const uint64_t *ring_in = rings + (size_t)(w > 0 ? w - 1 : 0) * kRing;  // written by warp w-1
     volatile int *cons = reinterpret_cast<volatile int *>(rings + (size_t)W * kRing);
     __shared__ __align__(16) uint64_t s_src[2 * kSrcRing];
     const uint32_t src_ring = (uint32_t)__cvta_generic_to_shared(s_src);
     const uint32_t pm_lane = (uint32_t)__cvta_generic_to_shared(pm + lane);
+    const uint32_t col_ring = (uint32_t)__cvta_generic_to_shared(colring);
 
     for (int c = 0; c < kMaxSigma; ++c) pm[c * 32 + lane] = 0u;
 
@@ -142,11 +150,49 @@ __global__ void __launch_bounds__(256, 1) k_pair_bp(const PairArgs P) {
         uint32_t cw_last = 0;       // this lane's carry-outs of the previous step
         uint32_t cin_cur = 0;       // carry-ins for this step (from the lane above)
         uint32_t gw = 0;            // lane 31: output word being assembled
-        uint32_t win[32], wnext[32];
         bool ok = true;
         bool bad31 = false;
-        load_window(P.boff, -(int64_t)kSkew * lane * C, P.S, win);
+        // lanes 0..7 copy one 32-column word of offsets (16 bytes each) per call
+        auto issue_cols = [&](int64_t wd) {
+            if (lane < 8 && wd < nwords) {
+                const int64_t col = wd * 32 + lane * 4;
+                const int64_t rem = P.S - col;
+                const int bytes = rem >= 4 ? 16 : (rem > 0 ? (int)rem * 4 : 0);
+                const uint32_t *src = P.boff + (bytes > 0 ? col : 0);
+                const uint32_t dst = col_ring + (uint32_t)(((wd % kColRing) * 32 + lane * 4) * 4);
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes)
+                             : "memory");
+            }
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        };
+        for (int d = 0; d < kColAhead; ++d) issue_cols(d);
+        // this lane's C offsets of chunk q from the ring (q may be out of range: value unused)
+        auto offs_of = [&](int64_t q, uint32_t (&o)[C]) {
+            const int64_t col = q * C;
+            const uint32_t addr = col_ring + (uint32_t)(((((col >> 5) % kColRing) + kColRing) % kColRing) * 128 +
+                                                        (col & 31) * 4);
+            if constexpr (C == 2) {
+                uint32_t x, y;
+                asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(x), "=r"(y) : "r"(addr));
+                o[0] = x;
+                o[1] = y;
+            } else {
+#pragma unroll
+                for (int k = 0; k < C / 4; ++k) {
+                    uint32_t x, y, z, v;
+                    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                                 : "=r"(x), "=r"(y), "=r"(z), "=r"(v) : "r"(addr + 16 * k));
+                    o[4 * k] = x;
+                    o[4 * k + 1] = y;
+                    o[4 * k + 2] = z;
+                    o[4 * k + 3] = v;
+                }
+            }
+        };
         for (int64_t u = 0; u < nouter; ++u) {
+            asm volatile("cp.async.wait_group %0;" ::"n"(kColAhead - 1) : "memory");
+            __syncwarp();
+            issue_cols(u + kColAhead);
             uint32_t srcw = 0;
             bool lok = !bad31;
             if (lane == 0 && u < nwords) {
@@ -176,20 +222,23 @@ __global__ void __launch_bounds__(256, 1) k_pair_bp(const PairArgs P) {
                 break;
             }
             const int64_t ubase = u * K;
-            const int64_t col0 = (ubase - (int64_t)kSkew * lane) * C;  // this lane's 32 columns
-            if (u + 1 < nouter) load_window(P.boff, col0 + 32, P.S, wnext);
             if (u >= u_fast0 && u < u_fast1) {
                 // ---------- steady state: all lanes hold full chunks ----------
+                uint32_t ocur[C], onext[C];
+                offs_of(ubase - (int64_t)kSkew * lane, ocur);
 #pragma unroll
                 for (int i = 0; i < K; ++i) {
+                    if (i + 1 < K) offs_of(ubase + i + 1 - (int64_t)kSkew * lane, onext);
                     const uint32_t recv = __shfl_up_sync(kFull, cw_last, 1);
                     uint32_t sr = (lane == 0) ? (srcw << (i * C)) : (cin_cur << (32 - C));
                     uint32_t cw = 0;
 #pragma unroll
                     for (int jj = 0; jj < C; ++jj) {
-                        const uint32_t M = lds_u32(pm_lane + win[i * C + jj]);
+                        const uint32_t M = lds_u32(pm_lane + ocur[jj]);
                         column31(Sv, Yv, sr, cw, M);
                     }
+#pragma unroll
+                    for (int jj = 0; jj < C; ++jj) ocur[jj] = onext[jj];
                     cw_last = cw;
                     cin_cur = recv;
                     gw |= cw << ((32 - C - (((i + kSkew) * C) & 31)) & 31);
@@ -217,12 +266,14 @@ __global__ void __launch_bounds__(256, 1) k_pair_bp(const PairArgs P) {
                     uint32_t sr = (lane == 0) ? (srcw << (i * C)) : (cin_cur << (32 - C));
                     uint32_t cw = 0;
                     const bool act = (q >= 0) && (q < nch);
+                    uint32_t oq[C];
+                    offs_of(q, oq);
                     if (act) {
                         if (q == nch - 1 && last_valid < C) {
 #pragma unroll
                             for (int jj = 0; jj < C; ++jj) {
                                 if (jj < last_valid) {
-                                    const uint32_t M = lds_u32(pm_lane + win[i * C + jj]);
+                                    const uint32_t M = lds_u32(pm_lane + oq[jj]);
                                     column31(Sv, Yv, sr, cw, M);
                                 }
                             }
@@ -230,7 +281,7 @@ __global__ void __launch_bounds__(256, 1) k_pair_bp(const PairArgs P) {
                         } else {
 #pragma unroll
                             for (int jj = 0; jj < C; ++jj) {
-                                const uint32_t M = lds_u32(pm_lane + win[i * C + jj]);
+                                const uint32_t M = lds_u32(pm_lane + oq[jj]);
                                 column31(Sv, Yv, sr, cw, M);
                             }
                         }
@@ -254,10 +305,9 @@ __global__ void __launch_bounds__(256, 1) k_pair_bp(const PairArgs P) {
                     }
                 }
             }
-#pragma unroll
-            for (int k = 0; k < 32; ++k) win[k] = wnext[k];
         }
-        if (w == 0 && lane == 0) asm volatile("cp.async.wait_all;" ::: "memory");
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        __syncwarp();
 
         if (ok && nreal > 0) P.right_bits[rbase / kLaneRows] = ~(Sv | Yv) & realmask;
 #pragma unroll
@@ -509,8 +559,8 @@ __global__ void k_int_peak(int op, int iters, uint32_t *sink) {
 }  // namespace
 
 size_t pair_smem_bytes(int warps, int /*sigma*/) {
-    return (size_t)warps * kTableBytes + (size_t)warps * kRing * sizeof(uint64_t) +
-           (size_t)warps * sizeof(int) + 16;
+    return (size_t)warps * kTableBytes + (size_t)warps * kColRing * 128 +
+           (size_t)warps * kRing * sizeof(uint64_t) + (size_t)warps * sizeof(int) + 16;
 }
 
 int pair_max_warps(int sigma) {
@@ -546,8 +596,6 @@ int pair_occupancy(int C, int warps) {
         case 2: return occ_c<2>(warps);
         case 4: return occ_c<4>(warps);
         case 8: return occ_c<8>(warps);
-        case 16: return occ_c<16>(warps);
-        case 32: return occ_c<32>(warps);
         default: return 0;
     }
 }
@@ -557,8 +605,6 @@ cudaError_t launch_pair_bp(const PairArgs &p, int C, int warps, int grid, cudaSt
         case 2: return launch_c<2>(p, warps, grid, st);
         case 4: return launch_c<4>(p, warps, grid, st);
         case 8: return launch_c<8>(p, warps, grid, st);
-        case 16: return launch_c<16>(p, warps, grid, st);
-        case 32: return launch_c<32>(p, warps, grid, st);
         default: return cudaErrorInvalidValue;
     }
 }

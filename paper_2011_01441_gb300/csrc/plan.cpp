@@ -171,25 +171,14 @@ bool plan_pair(int64_t n, int64_t m, int sms, const PairPlanOptions &o, PairPlan
     out.transpose = o.orient == 2 || (o.orient == 0 && m > n);
     out.L = out.transpose ? m : n;
     out.S = out.transpose ? n : m;
-    // chunk width: minimise the critical path of the lane pipeline, (S + 2*C*lanes) column
-    // steps of ~c_col cycles plus ~c_step cycles of per-chunk overhead (the carry hand-off
-    // through a shuffle is hidden behind one chunk by the two-chunk lane skew)
-    if (o.chunk) {
-        out.C = o.chunk;
-    } else {
-        const double c_col = 8.0, c_step = 12.0;
-        const double lanes = (double)out.L / kPlanLaneRows;
-        double best = 1e300;
-        for (int C = 2; C <= 32; C *= 2) {
-            const double cost = ((double)out.S + 2.0 * C * lanes) * c_col + ((double)out.S / C + 2.0 * lanes) * c_step;
-            if (cost < best) {
-                best = cost;
-                out.C = C;
-            }
-        }
-    }
+    // chunk width: lane k of a strip trails lane 0 by 2k chunks, so the
+    // pipeline's fill grows with C while the per-chunk hand-off cost shrinks;
+    // measured on GB300 the hand-off is already hidden at C = 2, which then
+    // wins whenever the streamed side is long enough to amortise it.
+    out.C = o.chunk ? o.chunk : ((out.S >= 64) ? 2 : 4);
     const int64_t warps_total = (out.L + kPlanWarpRows - 1) / kPlanWarpRows;
-    int W = o.warps > 0 ? o.warps : 4;
+    // one warp per CTA strip unless the strips would not all be resident at once
+    int W = o.warps > 0 ? o.warps : 1;
     W = std::max(1, std::min(W, o.max_warps));
     if ((int64_t)W > warps_total) W = (int)warps_total;
     int64_t nstrips = (warps_total + W - 1) / W;

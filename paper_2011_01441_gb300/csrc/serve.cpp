@@ -172,7 +172,7 @@ int launch_slot(ServeEngine *E, Slot &S) {
     int rc = run_batch(E->ctx, S.B, (const uint8_t *)S.a.ptr, S.a_off.data(), (const uint8_t *)S.b.ptr,
                        S.b_off.data(), np, (int32_t *)S.len.ptr, any_want ? (int32_t *)S.rows.ptr : nullptr,
                        S.row_off.data(), any_want ? (int32_t *)S.cols.ptr : nullptr, S.col_off.data(), S.stream,
-                       false, 4);
+                       false, 4, E->ctx->opt_alphabet);
     if (rc != PACO_OK) return rc;
     e = cudaMemcpyAsync(S.h_len, S.len.ptr, (size_t)np * 4, cudaMemcpyDeviceToHost, S.stream);
     if (e == cudaSuccess && any_want)

@@ -165,7 +165,7 @@ def test_pair_plan_balanced_strips(lib, n, m, sms):
     assert np.all(h <= pl["warps"] * 992)
     if h.size > 2:
         assert h[:-1].max() - h[:-1].min() <= 31  # the +-1 granule split of the p-way division
-    assert pl["chunk"] in (2, 4, 8, 16, 32)
+    assert pl["chunk"] in (2, 4, 8)
 
 
 def test_pair_plan_options(lib):

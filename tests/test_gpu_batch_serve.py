@@ -102,6 +102,24 @@ def test_batch_tall_pairs_chain_segments(ctx):
     check_batch(ctx, B, A, boundaries=True)
 
 
+def test_batch_declared_alphabet(ctx):
+    """A declared alphabet shrinks the match table; results are unchanged,
+    and a symbol outside it is reported (PACO_EINVAL) without a fault."""
+    A = [W.symbols(81, k, 600 + 50 * k, 4) for k in range(20)]
+    B = [W.mutate_rate(a, 4, 0.2, 82, k) for k, a in enumerate(A)]
+    ctx.set_option(P.OPT_ALPHABET, 4)
+    try:
+        check_batch(ctx, A, B, boundaries=True)
+        bad = [a.copy() for a in A]
+        bad[3][5] = 9
+        with pytest.raises(P.PacoError) as e:
+            run_batch(ctx, bad, B)
+        assert e.value.status == P.PACO_EINVAL
+        check_batch(ctx, A, B)
+    finally:
+        ctx.set_option(P.OPT_ALPHABET, 256)
+
+
 def test_batch_graph_replay_and_new_data(ctx):
     A, B = _mixed_pairs(31, 30, LENS)
     first = run_batch(ctx, A, B)

@@ -66,7 +66,7 @@ def test_alphabets(ctx, sigma):
     check(ctx, a, b)
 
 
-@pytest.mark.parametrize("chunk,warps", [(c, w) for c in (2, 4, 8, 16, 32) for w in (1, 3)] + [(8, 7), (4, 2)])
+@pytest.mark.parametrize("chunk,warps", [(c, w) for c in (2, 4, 8) for w in (1, 3, 6)] + [(4, 2)])
 def test_chunks_and_strip_heights(ctx, chunk, warps):
     # several CTA strips (inter-CTA chaining) and several warps (shared ring)
     a = W.symbols(chunk * 100 + warps, 0, 7000, 4)
