@@ -7,7 +7,7 @@ path over that pair: boundary preparation, the strip-pipeline kernel, and the
 two boundary prefixes.  Inputs are resident in HBM before timing; the 256 KB
 of inputs fit in L2, so L2 is flushed (a 512 MiB write) between timed steps.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--config mutated|small|skinny|batch]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--config mutated|small|skinny|batch|serve]
   python bench.py --impl reference ...   # the CPU oracle on a bounded sample
 
 Under torchrun each rank computes its own copy of the workload (independent
@@ -33,8 +33,15 @@ import numpy as np  # noqa: E402
 from paper_2011_01441_gb300 import workloads as W  # noqa: E402
 
 METRIC = "LCS GCUPS on 1 GB300, % of INT32 roofline; served p50/p99 latency vs plain"
-# lane-ops per 32-row column step of the bit-parallel tile (or, and, and-not, add-with-carry)
-OPS_PER_WORD_STEP = 4  # per 31-row lane word and column
+# Algorithmic integer lane-ops of one bit-parallel column step of a 31-row
+# word: X = V & M, the carry add V + X + c, V & ~M, and the final OR (the
+# recurrence of Eq. 1 in the bit-vector form of Allison-Dix / Hyyro).
+OPS_PER_WORD_STEP = 4
+# The per-cell work the roofline is defined on: Eq. 1 evaluated cell by cell
+# as h = max(max(up, left), diag + (a_i == b_j)) is 4 INT32 lane-ops (match,
+# add, max, max).  The bit-parallel kernels need only OPS_PER_WORD_STEP per
+# 31 cells, so they can exceed this cell-wise roofline; both are reported.
+CELL_OPS = 4
 
 
 def _dist():
@@ -42,6 +49,39 @@ def _dist():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def _init_dist(ws, local, backend="nccl"):
+    """One process per GPU (torchrun): join the process group when ws > 1."""
+    import torch
+    import torch.distributed as dist
+    if ws > 1 and not dist.is_initialized():
+        if backend == "nccl":
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        else:
+            dist.init_process_group(backend)
+
+
+def _max_over_ranks(x, device=None):
+    """The slowest rank's value (the timed region is the max over ranks)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.barrier()
+
+
+def weak_scaling_value(cells_per_rank, ws, steps, max_ms):
+    """Whole-job GCUPS: the cells all ranks processed over the slowest rank's time."""
+    return cells_per_rank * ws * steps / (max_ms * 1e-3) / 1e9
 
 
 def _workload(name):
@@ -117,6 +157,35 @@ def _peaks():
         return {}
 
 
+def _profiled_traffic(profile, sources):
+    """Per-launch DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum)
+    from a committed ncu summary under profiles/, only while the kernel's
+    sources still hash to the ones that were profiled; else None."""
+    import hashlib
+    try:
+        rec = {}
+        with open(os.path.join(ROOT, "profiles", profile)) as f:
+            for line in f:
+                k, _, v = line.partition(":")
+                if k.strip() in ("traffic_bytes_per_launch", "source_sha256"):
+                    rec[k.strip()] = v.strip()
+        h = hashlib.sha256()
+        for src in sources:
+            with open(os.path.join(ROOT, "paper_2011_01441_gb300", "csrc", src), "rb") as f:
+                h.update(f.read())
+        if rec.get("source_sha256") != h.hexdigest():
+            return None
+        return int(rec["traffic_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+# Dependency chain of one column of the bit-parallel step on a lane's critical
+# path: one LOP3 (4.4 cycles) then the carry add (about 4 cycles), measured
+# on GB300 with single-warp dependent chains.
+CHAIN_CYCLES_PER_COLUMN = 8.4
+
+
 def cpu_baseline_pair(a, b, budget_s=12.0):
     """The oracle as it stands, single thread, on the first rows of the same
     pair (a bounded sample), extrapolated to GCUPS."""
@@ -164,9 +233,7 @@ def run_gpu(args):
     import paper_2011_01441_gb300 as P
 
     ws, rank, local = _dist()
-    if ws > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    _init_dist(ws, local)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     P.load()
@@ -189,8 +256,7 @@ def run_gpu(args):
     ctx.sync()
     kernel_ms = []
     step_ms = []
-    if ws > 1:
-        torch.distributed.barrier()
+    _barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clocks:
         for _ in range(args.steps):
@@ -204,16 +270,11 @@ def run_gpu(args):
             step_ms.append(e0.elapsed_time(e1))
             kernel_ms.append(P.paco_last_kernel_ms(ctx)[0])
         torch.cuda.synchronize()
-    if ws > 1:
-        torch.distributed.barrier()
+    _barrier()
     ctx.sync()
-    tot_ms = sum(step_ms)
-    if ws > 1:
-        t = torch.tensor([tot_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        tot_ms = float(t.item())
+    tot_ms = _max_over_ranks(sum(step_ms), dev)
     cells = float(n) * m
-    value = cells * ws * args.steps / (tot_ms * 1e-3) / 1e9
+    value = weak_scaling_value(cells, ws, args.steps, tot_ms)
 
     # end to end through the host-buffer entry point (pinned host memory)
     ha = torch.from_numpy(pair.a).pin_memory()
@@ -235,13 +296,20 @@ def run_gpu(args):
     assert int(hlen.item()) == int(L.item())
 
     # roofline of the dominant kernel: measured integer-ALU issue rate
-    peak_ops = P.paco_measure_int_peak(ctx, 3)
+    peak_ops = P.paco_measure_int_peak(ctx, 0)
     kmed = statistics.median(kernel_ms)
     plan = P.paco_plan_pair(n, m, torch.cuda.get_device_properties(dev).multi_processor_count)
-    word_steps = (plan["L"] + 31) // 32 * plan["S"]
-    achieved = word_steps * OPS_PER_WORD_STEP / (kmed * 1e-3)
+    word_steps = (plan["L"] + 30) // 31 * plan["S"]
+    achieved_bp = word_steps * OPS_PER_WORD_STEP / (kmed * 1e-3)
+    achieved = cells * CELL_OPS / (kmed * 1e-3)
     peaks = _peaks()
     clk = clocks.summary()
+    sm_hz = (clk["sm_mhz"] if clk else 2070.0) * 1e6
+    lanes = (plan["L"] + 30) // 31
+    cp_steps = plan["S"] + 2 * plan["chunk"] * lanes
+    cp_ms = cp_steps * CHAIN_CYCLES_PER_COLUMN / sm_hz * 1e3
+    traffic = _profiled_traffic("k_pair_bp_pair131072_launches.md", ["pair_kernels.cu", "bp_device.cuh"]) \
+        if args.config == "mutated" else None
     if rank != 0:
         return
     line = {
@@ -253,9 +321,18 @@ def run_gpu(args):
                    "l2": "flushed between timed steps (512 MiB write)"},
         "kernel_ms_median": kmed,
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
-                     "unit": "Tops/s (int32 lane-ops)", "frac": achieved / peak_ops, "traffic": None,
-                     "kernel": "k_pair_bp", "ops_per_cell": OPS_PER_WORD_STEP / 32,
-                     "peak_source": "measured: paco_measure_int_peak(op=3), the kernel's column-step mix on all SMs"},
+                     "unit": "Tops/s (int32 lane-ops, 4 per cell)", "frac": achieved / peak_ops,
+                     "traffic": traffic, "kernel": "k_pair_bp", "ops_per_cell": CELL_OPS,
+                     "peak_source": "measured: paco_measure_int_peak(op=0), full-rate IADD3 on all SMs "
+                                    "(152 SMs x 128 lanes x clock), this run"},
+        "roofline_bitparallel": {"ops_per_cell": OPS_PER_WORD_STEP / 31, "achieved": achieved_bp / 1e12,
+                                 "frac": achieved_bp / peak_ops,
+                                 "note": "lane-ops the bit-parallel recurrence itself needs (4 per 31-row word "
+                                         "and column) over the same peak"},
+        "critical_path": {"bound": "dependency chain", "model_ms": cp_ms, "measured_ms": kmed,
+                          "frac": cp_ms / kmed, "column_steps": cp_steps,
+                          "cycles_per_column": CHAIN_CYCLES_PER_COLUMN,
+                          "note": "one lane streams all S columns; lanes trail by 2 chunks each"},
         "e2e": {"value": e2e_val, "unit": "GCUPS", "h2d_bytes_per_step": n + m,
                 "d2h_bytes_per_step": 4 * (n + 1) + 4 * (m + 1) + 4},
         "gpu_launches": 9 * args.steps,
@@ -298,30 +375,37 @@ def run_batch_bench(args):
     cells = bt.cells()
     value = cells * args.steps / (sum(ms) * 1e-3) / 1e9
     # plain: one pair per launch on one stream, same pairs
+    plain_s = float("nan")
     lens = torch.empty(1, dtype=torch.int32, device="cuda")
-    views = [(da[bt.a_off[k]:bt.a_off[k + 1]], db[bt.b_off[k]:bt.b_off[k + 1]]) for k in range(bt.npairs)]
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for a, b in views:
-        P.paco_lcs_length(ctx, a, b, out=lens)
-    torch.cuda.synchronize()
-    plain_s = time.perf_counter() - t0
+    if not args.no_plain:
+        views = [(da[bt.a_off[k]:bt.a_off[k + 1]], db[bt.b_off[k]:bt.b_off[k + 1]]) for k in range(bt.npairs)]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for a, b in views:
+            P.paco_lcs_length(ctx, a, b, out=lens)
+        torch.cuda.synchronize()
+        plain_s = time.perf_counter() - t0
     peak_ops = P.paco_measure_int_peak(ctx, 0)
     med = statistics.median(ms)
     word_steps = sum(((max(n, m) + 30) // 31) * min(n, m) for n, m in zip(np.diff(bt.a_off), np.diff(bt.b_off)))
-    achieved = word_steps * OPS_PER_WORD_STEP / (med * 1e-3)
+    achieved_bp = word_steps * OPS_PER_WORD_STEP / (med * 1e-3)
+    achieved = cells * CELL_OPS / (med * 1e-3)
     line = {"metric": METRIC, "value": value, "unit": "GCUPS", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": sum(ms) / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": bt.name + " (seed 4)", "pairs": bt.npairs, "cells": cells,
                        "engine": "batch graph, warp jobs", "alphabet": 4, "chunk": P.paco_last_batch_chunk(ctx) if hasattr(P, "paco_last_batch_chunk") else None,
                        "l2": "flushed between timed steps"},
-            "plain_one_pair_per_launch": {"value": cells / plain_s / 1e9, "unit": "GCUPS",
-                                          "seconds": plain_s},
+            "plain_one_pair_per_launch": None if args.no_plain else
+            {"value": cells / plain_s / 1e9, "unit": "GCUPS", "seconds": plain_s},
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
-                         "unit": "Tops/s (int32 lane-ops)", "frac": achieved / peak_ops,
-                         "kernel": "k_batch", "ops_per_cell": OPS_PER_WORD_STEP / 31,
+                         "unit": "Tops/s (int32 lane-ops, 4 per cell)", "frac": achieved / peak_ops,
+                         "traffic": _profiled_traffic("k_batch_batch4096_full.md", ["batch.cu", "bp_device.cuh"]),
+                         "duration": "whole step (column offsets + k_batch + prefixes), an upper bound on k_batch",
+                         "kernel": "k_batch", "ops_per_cell": CELL_OPS,
                          "peak_source": "measured: paco_measure_int_peak(op=0), full-rate IADD3 on all SMs"},
+            "roofline_bitparallel": {"ops_per_cell": OPS_PER_WORD_STEP / 31, "achieved": achieved_bp / 1e12,
+                                     "frac": achieved_bp / peak_ops},
             "clocks": clocks.summary()}
     print(json.dumps(line), flush=True)
     ctx.close()
@@ -421,6 +505,7 @@ def main():
     ap.add_argument("--config", default="mutated", choices=["mutated", "small", "skinny", "batch", "serve"])
     ap.add_argument("--requests", type=int, default=3000, help="serving: requests taken from the stream")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true", help="batch: skip the one-pair-per-launch comparison")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
