@@ -122,7 +122,7 @@ void paco_ctx_destroy(paco_ctx *ctx) {
     serve_shutdown(ctx);
     cudaDeviceSynchronize();
     batch_release(ctx);
-    for (DevBuf *b : {&ctx->small, &ctx->hbuf, &ctx->lbits, &ctx->rbits, &ctx->rows, &ctx->sums, &ctx->boff,
+    for (DevBuf *b : {&ctx->small, &ctx->hbuf, &ctx->lbits, &ctx->rbits, &ctx->rows, &ctx->sums,
                       &ctx->h_a, &ctx->h_b, &ctx->h_top, &ctx->h_left, &ctx->h_row, &ctx->h_col,
                       &ctx->h_len}) {
         if (b->ptr) cudaFree(b->ptr);

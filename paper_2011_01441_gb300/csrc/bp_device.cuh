@@ -134,6 +134,43 @@ static __device__ __forceinline__ void column31(uint32_t &S, uint32_t &Y, uint32
     cw = __funnelshift_l(A, cw, 1);
 }
 
+// The same column with bit 31 of S | Y held at 1 (rows live in bits 0..30).
+// Then bit 31 of V + X + c is 1 + 0 + (carry out of row 30), so the carry
+// flag of the 32-bit add is the lane's carry out; it is shifted straight
+// into cw by a second add-with-carry, and V' = S' | Y' keeps bit 31 set
+// through Y' = (S | Y) & ~M (M has no bit 31).
+//   V = S | Y, X = (S|Y) & M, Y' = (S|Y) & ~M                  (three LOP3)
+//   CC = top bit of sr; S' = V + X + CC, CC = carry out; cw = 2 cw + CC
+static __device__ __forceinline__ void column31c(uint32_t &S, uint32_t &Y, uint32_t &sr, uint32_t &cw,
+                                          uint32_t M) {
+    uint32_t V, X, Yn;
+    asm("lop3.b32 %0, %1, %2, 0, 0xFC;" : "=r"(V) : "r"(S), "r"(Y));
+    asm("lop3.b32 %0, %1, %2, %3, 0xA8;" : "=r"(X) : "r"(S), "r"(Y), "r"(M));
+    asm("lop3.b32 %0, %1, %2, %3, 0x54;" : "=r"(Yn) : "r"(S), "r"(Y), "r"(M));
+    asm("{\n\t"
+        "add.cc.u32 %0, %0, %0;\n\t"
+        "addc.cc.u32 %1, %3, %4;\n\t"
+        "addc.u32 %2, %2, %2;\n\t"
+        "}"
+        : "+r"(sr), "=r"(S), "+r"(cw)
+        : "r"(V), "r"(X));
+    Y = Yn;
+}
+
+static __device__ __forceinline__ int ld_acquire_shared(uint32_t addr) {
+    int v;
+    asm volatile("ld.acquire.cta.shared.s32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+    return v;
+}
+static __device__ __forceinline__ void st_release_shared(uint32_t addr, int v) {
+    asm volatile("st.release.cta.shared.s32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+static __device__ __forceinline__ int ld_volatile_shared(uint32_t addr) {
+    int v;
+    asm volatile("ld.volatile.shared.s32 %0, [%1];" : "=r"(v) : "r"(addr));
+    return v;
+}
+
 // The 32 column offsets [col0, col0 + 32) of a lane's word; columns outside
 // [0, S) read as 0 (their steps are inactive).
 static __device__ __forceinline__ uint2 ldg_v2(const void *p) {

@@ -35,7 +35,7 @@ struct paco_ctx {
     // small: [0] error word, [1] ticket, sink from byte 1024
     DevBuf small;
     // single-pair scratch
-    DevBuf hbuf, lbits, rbits, rows, sums, boff;
+    DevBuf hbuf, lbits, rbits, rows, sums;
     // staging for the host-buffer entry point
     DevBuf h_a, h_b, h_top, h_left, h_row, h_col, h_len;
     uint32_t epoch = 0;

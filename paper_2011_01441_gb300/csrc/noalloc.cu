@@ -7,8 +7,8 @@
 // re-entered), or a latency-critical loop where cudaMalloc/cudaFree would
 // synchronise the whole device.  This entry point serves them: the caller
 // passes device inputs and outputs only, and all scratch the strip pipeline
-// needs (boundary step bits, tagged carry rows, column-table offsets, the
-// ticket and error words) lives in one file-scope __device__ array of fixed
+// needs (boundary step bits, tagged carry rows, the ticket and error
+// words) lives in one file-scope __device__ array of fixed
 // size that every GPU loading this library keeps until the process exits.
 //
 // The array is shared by all calls on a device and keeps the previous call's
@@ -104,8 +104,6 @@ extern "C" int paco_lcs_boundaries_static(const uint8_t *a, int64_t n, const uin
     used = align_up(used + (size_t)lwords * 4 + 16);
     const size_t off_rbits = used;
     used = align_up(used + (size_t)rwords * 4 + 16);
-    const size_t off_boff = used;
-    used = align_up(used + (size_t)S * 4 + 64);
     const size_t off_sums = used;
     used = align_up(used + (size_t)nblocks * 8 * 2);
     if (used > kStaticScratchBytes) return PACO_EINVAL;  // table too large for the fixed scratch
@@ -119,13 +117,11 @@ extern "C" int paco_lcs_boundaries_static(const uint8_t *a, int64_t n, const uin
     uint64_t *hbuf = (uint64_t *)(scr + off_hbuf);
     e = launch_boundary_bits(nullptr, L, (uint32_t *)(scr + off_lbits), nullptr, epoch, nullptr, small + 1, st);
     if (e == cudaSuccess) e = launch_boundary_bits(nullptr, S, nullptr, hbuf, epoch, nullptr, small + 1, st);
-    if (e == cudaSuccess) e = launch_column_offsets(kb, S, (uint32_t *)(scr + off_boff), st);
     if (e != cudaSuccess) return PACO_EDEVICE;
 
     PairArgs P;
     P.a = ka;
     P.b = kb;
-    P.boff = (const uint32_t *)(scr + off_boff);
     P.L = L;
     P.S = S;
     P.nchunks = (S + pl.C - 1) / pl.C;

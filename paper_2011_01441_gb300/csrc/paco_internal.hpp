@@ -35,7 +35,6 @@ constexpr int kWarpRows = 31 * 32;
 struct PairArgs {
     const uint8_t *a;            // row string (bits), length L
     const uint8_t *b;            // column string (streamed), length S
-    const uint32_t *boff;        // S byte offsets of the columns' match-table rows
     int64_t L, S;
     int64_t nchunks;             // ceil(S / C)
     int64_t nwords;              // ceil(S / 32): words per carry row
@@ -55,7 +54,7 @@ struct PairArgs {
 };
 
 // Launch helpers (defined in pair_kernels.cu).
-size_t pair_smem_bytes(int warps, int sigma);
+size_t pair_smem_bytes(int warps, int C);  // dynamic shared memory of one CTA
 int pair_max_warps(int sigma);
 int pair_occupancy(int C, int warps);  // resident CTAs per SM
 cudaError_t launch_pair_bp(const PairArgs &p, int C, int warps, int grid, cudaStream_t st);
@@ -71,7 +70,6 @@ cudaError_t launch_bits_prefix(const uint32_t *bits, const uint64_t *tagged, int
                                const int32_t *base_ptr, int64_t base_index,
                                int32_t *out, int32_t *len_out,
                                PrefixScratch &scr, cudaStream_t st);
-cudaError_t launch_column_offsets(const uint8_t *b, int64_t S, uint32_t *boff, cudaStream_t st);
 // n == 0 or m == 0 tables: copy/zero the boundaries.
 cudaError_t launch_degenerate(const int32_t *top, const int32_t *left, int64_t n, int64_t m,
                               int32_t *bottom_row, int32_t *right_col, int32_t *len,

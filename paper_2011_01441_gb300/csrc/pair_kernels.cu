@@ -2,22 +2,27 @@
 //
 // The table of Eq. (1) (Tang & Gao, Sec. "PACO LCS") is computed on its
 // unit steps: in an LCS table neighbouring entries differ by 0 or 1, so a
-// column of 32 rows is one 32-bit word V (bit r set when H[r+1][j] ==
+// column of R rows is one R-bit word V (bit r set when H[r+1][j] ==
 // H[r][j], i.e. no vertical step) and the horizontal step between columns
 // at the word's top and bottom rows is one carry bit.  With M the rows whose
 // symbol equals b[j], one column of Eq. (1) is
 //
-//     V' = (V + (V & M) + carry_in) | (V & ~M),   carry_out = bit 32 of the sum
+//     V' = (V + (V & M) + carry_in) | (V & ~M),   carry_out = carry of the sum
 //
 // (the bit-vector form of Allison & Dix 1986 / Crochemore et al. 2001 /
 // Hyyrö 2004; carry_in is the top row's horizontal step at column j and
-// carry_out the bottom row's).  A warp holds 32 lanes x 32 rows; each lane
-// hands the carry bits of a chunk of C columns to the lane below through
-// __shfl_up_sync, warps of one CTA strip chain through a shared-memory ring,
-// and CTA strips chain through global memory with epoch-tagged words.  The
-// PACO execution phase (regions run in anti-diagonal order, each waiting only
-// on its neighbours, no global barrier) is this pipeline: lane g of strip s
-// works on chunk q at step q + g.
+// carry_out the bottom row's).  A lane holds R = 31 rows (bit 31 of the word
+// stays set, so the carry flag of the 32-bit add is the carry out); a warp
+// holds 32 lanes x 31 rows, and each lane hands the carry bits of a chunk of
+// C columns to the lane below through __shfl_up_sync.  Warps of one CTA
+// strip chain through a shared-memory ring, and CTA strips chain through
+// global memory with epoch-tagged words.  One extra warp per CTA produces:
+// it turns the column string into match-table offsets and polls the strip
+// above for its carry words, both into shared rings, so the compute warps
+// never wait on global memory.  The PACO execution phase (regions run in
+// anti-diagonal order, each waiting only on its neighbours, no global
+// barrier) is this pipeline: lane g of strip s works on chunk q at step
+// q + 2g.
 #include "paco_internal.hpp"
 #include "bp_device.cuh"
 
@@ -33,40 +38,92 @@ using namespace dev;
 // carry word a lane receives from the lane above (one __shfl_up_sync per
 // step) was produced a full step before it is needed.
 constexpr int kSkew = 2;
-// Input-word ring of warp 0 (pairs of tagged words) and its prefetch depth.
-constexpr int kSrcRing = 8;
-constexpr int kSrcAhead = 4;
-// Column offsets reach each warp through a shared ring of kColRing 32-column
-// words, copied by cp.async kColAhead words ahead of lane 0 (the oldest word
-// still read, by lane 31, is at most 2*31*8/32 + 1 = 17 words behind).
-constexpr int kColRing = 32;
-constexpr int kColAhead = 8;
+// Warp 0's input carry words pass through a shared ring of kSrcSlots words.
+constexpr int kSrcSlots = 64;
+// Column-word lag of the oldest word a warp still reads behind the word its
+// lane 0 is on: lane 31 trails lane 0 by kSkew * 31 chunks.
+__host__ __device__ constexpr int col_lag_words(int C) { return (kSkew * 31 * C + 31) / 32 + 1; }
+// Column-offset ring slots (a power of two) for C and W compute warps: the
+// lag of the last warp behind the first, the in-warp lag and some lookahead.
+__host__ __device__ constexpr int col_slots(int C, int W) {
+    const int need = col_lag_words(C) + 4 + (W - 1) * (col_lag_words(C) + 2) + 8;
+    int r = 32;
+    while (r < need) r <<= 1;
+    return r;
+}
+
+// Shared-memory layout of one CTA: W match tables, the column-offset ring
+// (slots + two mirror slots, so a lane's window of the next 32 + 2C columns
+// never wraps), the
+// input ring of warp 0, the rings between consecutive warps, counters.
+struct PairSmem {
+    uint32_t tables, colring, srcring, rings, ctrl, bytes;
+};
+__host__ __device__ inline PairSmem pair_smem_layout(int W, int C) {
+    PairSmem L;
+    L.tables = 0;
+    L.colring = (uint32_t)(W * kTableBytes);
+    L.srcring = L.colring + (uint32_t)(col_slots(C, W) + 2) * 128u;
+    L.rings = L.srcring + (uint32_t)kSrcSlots * 4u;
+    L.ctrl = L.rings + (uint32_t)(W * kRing * 8);
+    L.bytes = L.ctrl + (uint32_t)(2 + W) * 4u + 16u;
+    return L;
+}
+
+// Compute warps wait here (uniformly: every lane reads the same words) when
+// the producer or the warp above is behind.  Bounded: false on a timeout or
+// a raised error.
+static __device__ __noinline__ bool wait_inputs(uint32_t prod_cols, uint32_t prod_src, int need_c,
+                                                int need_s, const uint64_t *ring_word, uint32_t tag,
+                                                int *err, long long limit) {
+    const uint64_t t0 = global_ns();
+    bool ok = true;
+    for (;;) {
+        bool ready = ld_acquire_shared(prod_cols) >= need_c;
+        if (need_s > 0) ready = ready && ld_acquire_shared(prod_src) >= need_s;
+        if (ring_word) ready = ready && (uint32_t)(*reinterpret_cast<const volatile uint64_t *>(ring_word) >> 32) == tag;
+        if (ready) break;
+        if (ld_relaxed_i32(err) != 0) { ok = false; break; }
+        if ((long long)(global_ns() - t0) > limit) {
+            raise_error(err, kEtimeout);
+            ok = false;
+            break;
+        }
+    }
+    return __all_sync(kFull, ok);
+}
 
 template <int C>
 __global__ void __launch_bounds__(256, 1) k_pair_bp(const PairArgs P) {
-    static_assert(C == 2 || C == 4 || C == 8, "the column ring covers lane lags up to 17 words");
+    static_assert(C == 2 || C == 4 || C == 8, "chunk widths 2, 4 and 8");
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_strip;
-    const int W = blockDim.x >> 5;
+    const int W = (int)(blockDim.x >> 5) - 1;  // compute warps; warp W produces
     const int w = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    uint32_t *pm = reinterpret_cast<uint32_t *>(smem + (size_t)w * kTableBytes);
-    uint32_t *colring = reinterpret_cast<uint32_t *>(smem + (size_t)W * kTableBytes) + (size_t)w * kColRing * 32;
-    uint64_t *rings = reinterpret_cast<uint64_t *>(smem + (size_t)W * kTableBytes + (size_t)W * kColRing * 128);
+    const PairSmem lay = pair_smem_layout(W, C);
+    const int R = col_slots(C, W);
+    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
+    const uint32_t col_ring = sbase + lay.colring;
+    const uint32_t src_ring = sbase + lay.srcring;
+    const uint32_t prod_cols = sbase + lay.ctrl, prod_src = prod_cols + 4, cons0 = prod_cols + 8;
+    uint64_t *rings = reinterpret_cast<uint64_t *>(smem + lay.rings);
     uint64_t *ring_out = rings + (size_t)w * kRing;                       // read by warp w+1
     const uint64_t *ring_in = rings + (size_t)(w > 0 ? w - 1 : 0) * kRing;  // written by warp w-1
-    volatile int *cons = reinterpret_cast<volatile int *>(rings + (size_t)W * kRing);
-    __shared__ __align__(16) uint64_t s_src[2 * kSrcRing];
-    const uint32_t src_ring = (uint32_t)__cvta_generic_to_shared(s_src);
+    volatile int *cons = reinterpret_cast<volatile int *>(smem + lay.ctrl + 8);
+    uint32_t *pm = reinterpret_cast<uint32_t *>(smem + (size_t)(w < W ? w : 0) * kTableBytes);
     const uint32_t pm_lane = (uint32_t)__cvta_generic_to_shared(pm + lane);
-    const uint32_t col_ring = (uint32_t)__cvta_generic_to_shared(colring);
 
-    for (int c = 0; c < kMaxSigma; ++c) pm[c * 32 + lane] = 0u;
+    if (w < W)
+        for (int c = 0; c < kMaxSigma; ++c) pm[c * 32 + lane] = 0u;
+    // every ring slot holds a valid table offset from the start
+    for (int i = threadIdx.x; i < (R + 2) * 32; i += blockDim.x)
+        reinterpret_cast<uint32_t *>(smem + lay.colring)[i] = 0u;
 
     constexpr int K = 32 / C;                      // steps per 32-column word
-    constexpr uint32_t cmask = (C == 32) ? kFull : ((1u << C) - 1u);
     constexpr int kLag = kSkew * 31;               // chunks lane 31 trails lane 0
     constexpr int kFlushStep = (kLag - 1) % K;     // step at which lane 31 completes a word
+    constexpr int kLagW = col_lag_words(C);
     const int64_t nch = P.nchunks;
     const int last_valid = (int)(P.S - (nch - 1) * C);
     const int64_t nch_full = (last_valid == C) ? nch : nch - 1;
@@ -74,7 +131,6 @@ __global__ void __launch_bounds__(256, 1) k_pair_bp(const PairArgs P) {
     const int64_t nouter = (nch + kLag + K - 1) / K;
     const int64_t u_fast0 = (kLag + K - 1) / K;
     const int64_t u_fast1 = nch_full / K;           // exclusive
-    const int64_t lwords = (P.L + 31) >> 5;
 
     for (;;) {
         __syncthreads();
@@ -82,13 +138,92 @@ __global__ void __launch_bounds__(256, 1) k_pair_bp(const PairArgs P) {
             int s = atomicAdd(P.ticket, 1);
             if (ld_relaxed_i32(P.err) != 0) s = P.nstrips;
             s_strip = s;
+            st_release_shared(prod_cols, 0);
+            st_release_shared(prod_src, 0);
         }
-        for (int i = lane; i < kRing; i += 32) ring_out[i] = 0ull;
-        if (lane == 0) cons[w] = 0;
+        if (w < W) {
+            for (int i = lane; i < kRing; i += 32) ring_out[i] = 0ull;
+            if (lane == 0) cons[w] = 0;
+        }
         __syncthreads();
         const int s = s_strip;
         if (s >= P.nstrips) break;
+        const uint64_t *src_row = P.hbuf + (size_t)s * P.hstride;
+        uint64_t *dst_row = P.hbuf + (size_t)(s + 1) * P.hstride;
+        const uint32_t want = (s == P.stall_strip) ? (P.epoch ^ 0x80000000u) : P.epoch;
 
+        if (w == W) {
+            // ---------------- producer warp ----------------
+            // Column offsets (symbol x 128 bytes) from b into the ring, as far
+            // ahead as the slowest compute warp allows; the strip's input
+            // carry words, polled in global memory 32 at a time, into the
+            // input ring of warp 0.
+            int64_t qc = 0, qs = 0;
+            int idle = 0;
+            uint64_t t_idle = global_ns();
+            while (qc < nwords || qs < nwords) {
+                bool progress = false;
+                int minc = cons[0];
+                for (int v = 1; v < W; ++v) minc = min(minc, cons[v]);
+                const int64_t lim_c = min(nwords, (int64_t)minc - 1 - kLagW + R);
+                if (qc < lim_c) {
+                    const int64_t qe = min(lim_c, qc + 4);
+                    uint32_t o[4];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const int64_t col = (qc + k) * 32 + lane;
+                        o[k] = (qc + k < qe && col < P.S) ? (uint32_t)__ldg(P.b + col) * 128u : 0u;
+                    }
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        if (qc + k < qe) {
+                            const uint32_t slot = (uint32_t)((qc + k) & (R - 1));
+                            uint32_t *ring = reinterpret_cast<uint32_t *>(smem + lay.colring);
+                            ring[slot * 32 + lane] = o[k];
+                            if (slot < 2) ring[((uint32_t)R + slot) * 32 + lane] = o[k];
+                        }
+                    }
+                    __syncwarp();
+                    if (lane == 0) st_release_shared(prod_cols, (int)qe);
+                    qc = qe;
+                    progress = true;
+                }
+                const int64_t lim_s = min(nwords, (int64_t)cons[0] + kSrcSlots - 1);
+                if (qs < lim_s) {
+                    const int64_t q = qs + lane;
+                    uint64_t v = 0;
+                    bool rd = false;
+                    if (q < lim_s) {
+                        v = ld_relaxed_u64(src_row + q);
+                        rd = (uint32_t)(v >> 32) == want;
+                    }
+                    const uint32_t bal = __ballot_sync(kFull, rd);
+                    const int n = (bal == kFull) ? 32 : (__ffs(~bal) - 1);
+                    if (lane < n)
+                        reinterpret_cast<uint32_t *>(smem + lay.srcring)[q & (kSrcSlots - 1)] = (uint32_t)v;
+                    if (n > 0) {
+                        __syncwarp();
+                        qs += n;
+                        if (lane == 0) st_release_shared(prod_src, (int)qs);
+                        progress = true;
+                    }
+                }
+                if (progress) {
+                    t_idle = global_ns();
+                    idle = 0;
+                } else {
+                    if (ld_relaxed_i32(P.err) != 0) break;
+                    if ((long long)(global_ns() - t_idle) > P.wait_limit_ns) {
+                        raise_error(P.err, kEtimeout);
+                        break;
+                    }
+                    if (++idle > 64) __nanosleep(64);  // spin first: the hand-off is on the critical path
+                }
+            }
+            continue;
+        }
+
+        // ---------------- compute warps ----------------
         int64_t row0, row1;
         if (P.strip_row0) {
             row0 = P.strip_row0[s];
@@ -117,144 +252,118 @@ __global__ void __launch_bounds__(256, 1) k_pair_bp(const PairArgs P) {
                 pm[ch * 32 + lane] |= 1u << r;
             }
         }
-        // V from the first column's vertical steps (bit set = no step); padding rows 1
-        uint32_t Sv = kK31, Yv = 0;
+        // V from the first column's vertical steps (bit set = no step),
+        // padding rows 1, bit 31 held at 1
+        uint32_t Sv = 0xffffffffu, Yv = 0;
         if (nreal > 0) {
+            const int64_t lwords = (P.L + 31) >> 5;
             const int64_t wi = rbase >> 5;
             const uint32_t lo = __ldg(P.left_bits + wi);
             const uint32_t hi = (wi + 1 < lwords) ? __ldg(P.left_bits + wi + 1) : 0u;
             const uint32_t steps = __funnelshift_r(lo, hi, (uint32_t)(rbase & 31)) & realmask;
-            Sv = (~steps) & kK31;
+            Sv = ~steps;
         }
         __syncwarp();
 
-        const uint64_t *src_row = P.hbuf + (size_t)s * P.hstride;
-        uint64_t *dst_row = P.hbuf + (size_t)(s + 1) * P.hstride;
-        const uint32_t want = (s == P.stall_strip) ? (P.epoch ^ 0x80000000u) : P.epoch;
-        // Warp 0, lane 0: the strip's input words arrive through a shared
-        // ring filled by cp.async two words at a time, kSrcAhead pairs ahead,
-        // so no register waits on an L2 round trip; a word whose tag is not
-        // yet the launch epoch (not yet published) is polled in global memory.
-        const int64_t npairs = (nwords + 1) >> 1;
-        auto issue_pair = [&](int64_t pr) {
-            if (pr < npairs) {
-                const uint32_t dst = src_ring + (uint32_t)((pr % kSrcRing) * 16);
-                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src_row + 2 * pr)
-                             : "memory");
-            }
-            asm volatile("cp.async.commit_group;" ::: "memory");
-        };
-        if (w == 0 && lane == 0)
-            for (int d = 0; d < kSrcAhead; ++d) issue_pair(d);
-        uint64_t ring_pf = 0;       // warps w > 0, lane 0: next ring word
-        uint32_t cw_last = 0;       // this lane's carry-outs of the previous step
-        uint32_t cin_cur = 0;       // carry-ins for this step (from the lane above)
-        uint32_t gw = 0;            // lane 31: output word being assembled
+        uint32_t cw = 0;        // this lane's carry-outs, newest in bit 0 (never reset)
+        uint32_t cin_cur = 0;   // the lane above's carry word for this step (sent two steps ago)
+        uint32_t cin_nxt = 0;   // ... and for the next step
+        uint32_t sr = 0;        // carry-ins, next one in bit 31
+        uint32_t Mcur[C];       // steady state: this step's match words
+        uint32_t onext[C];      // steady state: the next step's column offsets
         bool ok = true;
-        bool bad31 = false;
-        // lanes 0..7 copy one 32-column word of offsets (16 bytes each) per call
-        auto issue_cols = [&](int64_t wd) {
-            if (lane < 8 && wd < nwords) {
-                const int64_t col = wd * 32 + lane * 4;
-                const int64_t rem = P.S - col;
-                const int bytes = rem >= 4 ? 16 : (rem > 0 ? (int)rem * 4 : 0);
-                const uint32_t *src = P.boff + (bytes > 0 ? col : 0);
-                const uint32_t dst = col_ring + (uint32_t)(((wd % kColRing) * 32 + lane * 4) * 4);
-                asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes)
-                             : "memory");
-            }
-            asm volatile("cp.async.commit_group;" ::: "memory");
-        };
-        for (int d = 0; d < kColAhead; ++d) issue_cols(d);
-        // this lane's C offsets of chunk q from the ring (q may be out of range: value unused)
-        auto offs_of = [&](int64_t q, uint32_t (&o)[C]) {
-            const int64_t col = q * C;
-            const uint32_t addr = col_ring + (uint32_t)(((((col >> 5) % kColRing) + kColRing) % kColRing) * 128 +
-                                                        (col & 31) * 4);
-            if constexpr (C == 2) {
-                uint32_t x, y;
-                asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(x), "=r"(y) : "r"(addr));
-                o[0] = x;
-                o[1] = y;
-            } else {
-#pragma unroll
-                for (int k = 0; k < C / 4; ++k) {
-                    uint32_t x, y, z, v;
-                    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
-                                 : "=r"(x), "=r"(y), "=r"(z), "=r"(v) : "r"(addr + 16 * k));
-                    o[4 * k] = x;
-                    o[4 * k + 1] = y;
-                    o[4 * k + 2] = z;
-                    o[4 * k + 3] = v;
-                }
-            }
-        };
+        const uint32_t ring_tag0 = 1;
         for (int64_t u = 0; u < nouter; ++u) {
-            asm volatile("cp.async.wait_group %0;" ::"n"(kColAhead - 1) : "memory");
-            __syncwarp();
-            issue_cols(u + kColAhead);
+            // inputs of this word: column offsets up to word u+1, the input carry word u
+            const int need_c = (int)min(u + 2, nwords);
+            const int need_s = (w == 0 && u < nwords) ? (int)(u + 1) : 0;
+            const uint64_t *rw = (w > 0 && u < nwords) ? ring_in + (u % kRing) : nullptr;
             uint32_t srcw = 0;
-            bool lok = !bad31;
-            if (lane == 0 && u < nwords) {
-                if (w == 0) {
-                    if ((u & 1) == 0) {
-                        asm volatile("cp.async.wait_group %0;" ::"n"(kSrcAhead - 1) : "memory");
-                        issue_pair((u >> 1) + kSrcAhead);
-                    }
-                    const uint32_t slot = src_ring + (uint32_t)((((u >> 1) % kSrcRing) * 16) + (u & 1) * 8);
-                    uint64_t v;
-                    asm volatile("ld.shared.u64 %0, [%1];" : "=l"(v) : "r"(slot) : "memory");
-                    if ((uint32_t)(v >> 32) != want)
-                        v = poll_global_lane(src_row + u, want, P.err, P.wait_limit_ns, lok);
-                    srcw = (uint32_t)v;
-                } else {
-                    uint64_t v = ring_pf;
-                    if ((uint32_t)(v >> 32) != (uint32_t)(u + 1))
-                        v = poll_ring_lane(ring_in, u, P.err, P.wait_limit_ns, lok);
-                    srcw = (uint32_t)v;
-                    cons[w] = (int)(u + 1);
-                    if (u + 1 < nwords)
-                        ring_pf = reinterpret_cast<const volatile uint64_t *>(ring_in)[(u + 1) % kRing];
+            {
+                bool ready = ld_acquire_shared(prod_cols) >= need_c;
+                if (need_s) ready = ready && ld_acquire_shared(prod_src) >= need_s;
+                uint64_t rv = 0;
+                if (rw) {
+                    rv = *reinterpret_cast<const volatile uint64_t *>(rw);
+                    ready = ready && (uint32_t)(rv >> 32) == (uint32_t)(u + ring_tag0);
                 }
+                if (!ready) {
+                    if (!wait_inputs(prod_cols, prod_src, need_c, need_s, rw, (uint32_t)(u + ring_tag0), P.err,
+                                     P.wait_limit_ns)) {
+                        ok = false;
+                        break;
+                    }
+                    if (rw) rv = *reinterpret_cast<const volatile uint64_t *>(rw);
+                }
+                if (need_s) srcw = lds_u32(src_ring + (uint32_t)((u & (kSrcSlots - 1)) * 4));
+                else srcw = (uint32_t)rv;
             }
-            if (!__all_sync(kFull, lok)) {
-                ok = false;
-                break;
-            }
+            if (lane == 0) st_release_shared(cons0 + 4u * (uint32_t)w, (int)(u + 1));
             const int64_t ubase = u * K;
+            // this lane's column of step 0 and its place in the ring
+            const int64_t c0 = u * 32 - (int64_t)kSkew * C * lane;
+            const uint32_t cbase = col_ring + (uint32_t)(((c0 >> 5) & (R - 1)) * 128) + (uint32_t)((c0 & 31) * 4);
+            auto offs_at = [&](uint32_t addr, uint32_t (&o)[C]) {
+                if constexpr (C == 2) {
+                    uint32_t x, y;
+                    asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(x), "=r"(y) : "r"(addr));
+                    o[0] = x;
+                    o[1] = y;
+                } else {
+#pragma unroll
+                    for (int k = 0; k < C / 4; ++k) {
+                        uint32_t x, y, z, v;
+                        asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                                     : "=r"(x), "=r"(y), "=r"(z), "=r"(v) : "r"(addr + 16 * k));
+                        o[4 * k] = x;
+                        o[4 * k + 1] = y;
+                        o[4 * k + 2] = z;
+                        o[4 * k + 3] = v;
+                    }
+                }
+            };
+            if (lane == 0) sr = srcw;
             if (u >= u_fast0 && u < u_fast1) {
                 // ---------- steady state: all lanes hold full chunks ----------
-                uint32_t ocur[C], onext[C];
-                offs_of(ubase - (int64_t)kSkew * lane, ocur);
+                // Software pipeline: offsets two steps ahead, match words one
+                // step ahead, the carry hand-off after the step's columns (its
+                // result is used two steps later), so a warp issuing in order
+                // never waits on a shared load or a shuffle before a column.
+                if (u == u_fast0) {  // later words: carried over from the step before
+                    uint32_t o0[C];
+                    offs_at(cbase, o0);
+#pragma unroll
+                    for (int jj = 0; jj < C; ++jj) Mcur[jj] = lds_u32(pm_lane + o0[jj]);
+                    offs_at(cbase + (uint32_t)(C * 4), onext);
+                }
 #pragma unroll
                 for (int i = 0; i < K; ++i) {
-                    if (i + 1 < K) offs_of(ubase + i + 1 - (int64_t)kSkew * lane, onext);
-                    const uint32_t recv = __shfl_up_sync(kFull, cw_last, 1);
-                    uint32_t sr = (lane == 0) ? (srcw << (i * C)) : (cin_cur << (32 - C));
-                    uint32_t cw = 0;
+                    uint32_t onext2[C], Mnext[C];
+                    offs_at(cbase + (uint32_t)((i + 2) * C * 4), onext2);
+#pragma unroll
+                    for (int jj = 0; jj < C; ++jj) Mnext[jj] = lds_u32(pm_lane + onext[jj]);
+                    if (lane != 0) sr = cin_cur << (32 - C);
+#pragma unroll
+                    for (int jj = 0; jj < C; ++jj) column31c(Sv, Yv, sr, cw, Mcur[jj]);
+                    const uint32_t recv = __shfl_up_sync(kFull, cw, 1);
+                    cin_cur = cin_nxt;
+                    cin_nxt = recv;
 #pragma unroll
                     for (int jj = 0; jj < C; ++jj) {
-                        const uint32_t M = lds_u32(pm_lane + ocur[jj]);
-                        column31(Sv, Yv, sr, cw, M);
+                        Mcur[jj] = Mnext[jj];
+                        onext[jj] = onext2[jj];
                     }
-#pragma unroll
-                    for (int jj = 0; jj < C; ++jj) ocur[jj] = onext[jj];
-                    cw_last = cw;
-                    cin_cur = recv;
-                    gw |= cw << ((32 - C - (((i + kSkew) * C) & 31)) & 31);
-                    if (i == kFlushStep) {
-                        if (lane == 31) {
-                            const int64_t wq = ((ubase + i - kLag) * C) >> 5;
-                            if (w + 1 < W) {
-                                if (!wait_consumed(cons + w + 1, (int)(wq - kRing + 1), P.err, P.wait_limit_ns))
-                                    bad31 = true;
-                                reinterpret_cast<volatile uint64_t *>(ring_out)[wq % kRing] =
-                                    ((uint64_t)(uint32_t)(wq + 1) << 32) | gw;
-                            } else {
-                                st_relaxed_u64(dst_row + wq, ((uint64_t)P.epoch << 32) | gw);
-                            }
+                    if (i == kFlushStep && lane == 31) {
+                        const int64_t wq = ((ubase + i - kLag) * C) >> 5;
+                        if (w + 1 < W) {
+                            // on a timeout the error is raised and every later wait
+                            // returns at once, so the strip ends with its result void
+                            wait_consumed(cons + w + 1, (int)(wq - kRing + 1), P.err, P.wait_limit_ns);
+                            reinterpret_cast<volatile uint64_t *>(ring_out)[wq % kRing] =
+                                ((uint64_t)(uint32_t)(wq + ring_tag0) << 32) | cw;
+                        } else {
+                            st_relaxed_u64(dst_row + wq, ((uint64_t)P.epoch << 32) | cw);
                         }
-                        gw = 0;
                     }
                 }
             } else {
@@ -262,19 +371,17 @@ __global__ void __launch_bounds__(256, 1) k_pair_bp(const PairArgs P) {
 #pragma unroll
                 for (int i = 0; i < K; ++i) {
                     const int64_t q = ubase + i - (int64_t)kSkew * lane;
-                    const uint32_t recv = __shfl_up_sync(kFull, cw_last, 1);
-                    uint32_t sr = (lane == 0) ? (srcw << (i * C)) : (cin_cur << (32 - C));
-                    uint32_t cw = 0;
                     const bool act = (q >= 0) && (q < nch);
                     uint32_t oq[C];
-                    offs_of(q, oq);
+                    offs_at(cbase + (uint32_t)(i * C * 4), oq);
                     if (act) {
+                        if (lane != 0) sr = cin_cur << (32 - C);
                         if (q == nch - 1 && last_valid < C) {
 #pragma unroll
                             for (int jj = 0; jj < C; ++jj) {
                                 if (jj < last_valid) {
                                     const uint32_t M = lds_u32(pm_lane + oq[jj]);
-                                    column31(Sv, Yv, sr, cw, M);
+                                    column31c(Sv, Yv, sr, cw, M);
                                 }
                             }
                             cw <<= (C - last_valid);  // keep the chunk MSB-first
@@ -282,33 +389,29 @@ __global__ void __launch_bounds__(256, 1) k_pair_bp(const PairArgs P) {
 #pragma unroll
                             for (int jj = 0; jj < C; ++jj) {
                                 const uint32_t M = lds_u32(pm_lane + oq[jj]);
-                                column31(Sv, Yv, sr, cw, M);
+                                column31c(Sv, Yv, sr, cw, M);
                             }
                         }
                     }
-                    cw_last = cw;
-                    cin_cur = recv;
-                    if (lane == 31 && act) {
-                        gw |= cw << (32 - C - ((q * C) & 31));
-                        if (i == kFlushStep || q == nch - 1) {
-                            const int64_t wq = (q * C) >> 5;
-                            if (w + 1 < W) {
-                                if (!wait_consumed(cons + w + 1, (int)(wq - kRing + 1), P.err, P.wait_limit_ns))
-                                    bad31 = true;
-                                reinterpret_cast<volatile uint64_t *>(ring_out)[wq % kRing] =
-                                    ((uint64_t)(uint32_t)(wq + 1) << 32) | gw;
-                            } else {
-                                st_relaxed_u64(dst_row + wq, ((uint64_t)P.epoch << 32) | gw);
-                            }
-                            gw = 0;
+                    const uint32_t recv = __shfl_up_sync(kFull, cw, 1);
+                    cin_cur = cin_nxt;
+                    cin_nxt = recv;
+                    if (lane == 31 && act && (i == kFlushStep || q == nch - 1)) {
+                        const int64_t wq = (q * C) >> 5;
+                        const uint32_t gw = cw << ((32 - C - ((q * C) & 31)) & 31);
+                        if (w + 1 < W) {
+                            // on a timeout the error is raised and every later wait
+                            // returns at once, so the strip ends with its result void
+                            wait_consumed(cons + w + 1, (int)(wq - kRing + 1), P.err, P.wait_limit_ns);
+                            reinterpret_cast<volatile uint64_t *>(ring_out)[wq % kRing] =
+                                ((uint64_t)(uint32_t)(wq + ring_tag0) << 32) | gw;
+                        } else {
+                            st_relaxed_u64(dst_row + wq, ((uint64_t)P.epoch << 32) | gw);
                         }
                     }
                 }
             }
         }
-        asm volatile("cp.async.wait_all;" ::: "memory");
-        __syncwarp();
-
         if (ok && nreal > 0) P.right_bits[rbase / kLaneRows] = ~(Sv | Yv) & realmask;
 #pragma unroll
         for (int r = 0; r < kLaneRows; ++r) {
@@ -318,13 +421,6 @@ __global__ void __launch_bounds__(256, 1) k_pair_bp(const PairArgs P) {
             }
         }
     }
-}
-
-// Column string -> byte offsets of its symbols' rows in a warp's match table.
-__global__ void k_column_offsets(const uint8_t *b, int64_t S, uint32_t *boff) {
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < S;
-         j += (int64_t)gridDim.x * blockDim.x)
-        boff[j] = (uint32_t)b[j] * 32u * 4u;
 }
 
 // ---------------------------------------------------------------------------
@@ -558,35 +654,32 @@ __global__ void k_int_peak(int op, int iters, uint32_t *sink) {
 
 }  // namespace
 
-size_t pair_smem_bytes(int warps, int /*sigma*/) {
-    return (size_t)warps * kTableBytes + (size_t)warps * kColRing * 128 +
-           (size_t)warps * kRing * sizeof(uint64_t) + (size_t)warps * sizeof(int) + 16;
-}
+size_t pair_smem_bytes(int warps, int C) { return pair_smem_layout(warps, C).bytes; }
 
-int pair_max_warps(int sigma) {
-    int w = 1;
-    while (w < 32 && pair_smem_bytes(w + 1, sigma) <= 227 * 1024 - 64) ++w;
+int pair_max_warps(int /*sigma*/) {
+    int w = 1;  // the widest chunk (largest column ring) bounds every configuration
+    while (w < 7 && pair_smem_bytes(w + 1, 8) <= 227 * 1024 - 64) ++w;
     return w;
 }
 
 template <int C>
 static cudaError_t launch_c(const PairArgs &p, int warps, int grid, cudaStream_t st) {
-    const size_t smem = pair_smem_bytes(warps, p.sigma);
+    const size_t smem = pair_smem_bytes(warps, C);
     cudaError_t e = cudaFuncSetAttribute(k_pair_bp<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    k_pair_bp<C><<<grid, warps * 32, smem, st>>>(p);
+    k_pair_bp<C><<<grid, (warps + 1) * 32, smem, st>>>(p);  // + the producer warp
     return cudaGetLastError();
 }
 
 template <int C>
 static int occ_c(int warps) {
-    const size_t smem = pair_smem_bytes(warps, kMaxSigma);
+    const size_t smem = pair_smem_bytes(warps, C);
     if (cudaFuncSetAttribute(k_pair_bp<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return 0;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pair_bp<C>, warps * 32, smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pair_bp<C>, (warps + 1) * 32, smem) != cudaSuccess)
         return 0;
     return nb;
 }
@@ -650,12 +743,6 @@ cudaError_t launch_bits_prefix(const uint32_t *bits, const uint64_t *tagged, int
         k_prefix_pass3<31><<<(unsigned)nblocks, kPB, 0, st>>>(bits, tagged, nbits, scr.block_sums,
                                                               base_ptr, base_index, out, len_out);
     }
-    return cudaGetLastError();
-}
-
-cudaError_t launch_column_offsets(const uint8_t *b, int64_t S, uint32_t *boff, cudaStream_t st) {
-    const int grid = (int)min((int64_t)4096, (S + 255) / 256);
-    k_column_offsets<<<grid, 256, 0, st>>>(b, S, boff);
     return cudaGetLastError();
 }
 

@@ -94,7 +94,6 @@ int run_pair(paco_ctx *ctx, const uint8_t *a, int64_t n, const uint8_t *b, int64
     if ((rc = ensure_bytes(ctx, ctx->hbuf, (size_t)(pl.nstrips + 1) * hstride * 8 + 16)) != PACO_OK) return rc;
     if ((rc = ensure_bytes(ctx, ctx->lbits, (size_t)lwords * 4 + 16)) != PACO_OK) return rc;
     if ((rc = ensure_bytes(ctx, ctx->rbits, (size_t)rwords * 4 + 16)) != PACO_OK) return rc;
-    if ((rc = ensure_bytes(ctx, ctx->boff, (size_t)S * 4 + 64)) != PACO_OK) return rc;
     if ((rc = ensure_bytes(ctx, ctx->sums, (size_t)nblocks * 8 * 2)) != PACO_OK) return rc;
 
     const uint32_t epoch = next_epoch(ctx);
@@ -103,14 +102,12 @@ int run_pair(paco_ctx *ctx, const uint8_t *a, int64_t n, const uint8_t *b, int64
                              ctx->err_ptr(), st);
     if (e == cudaSuccess)
         e = launch_boundary_bits(ktop, S, nullptr, hbuf, epoch, kleft, ctx->err_ptr(), st);
-    if (e == cudaSuccess) e = launch_column_offsets(kb, S, (uint32_t *)ctx->boff.ptr, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ticket_ptr(), 0, sizeof(int), st);
     if (e != cudaSuccess) return set_cuda_error(ctx, e, "prepare boundaries");
 
     PairArgs P;
     P.a = ka;
     P.b = kb;
-    P.boff = (const uint32_t *)ctx->boff.ptr;
     P.L = L;
     P.S = S;
     P.nchunks = (S + pl.C - 1) / pl.C;
