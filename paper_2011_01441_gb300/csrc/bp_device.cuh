@@ -157,6 +157,16 @@ static __device__ __forceinline__ void column31c(uint32_t &S, uint32_t &Y, uint3
     Y = Yn;
 }
 
+// Predicated stores (no branch, so no divergence for a one-lane store).
+static __device__ __forceinline__ void st_relaxed_u64_if(bool p, uint64_t *ptr, uint64_t v) {
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %0, 0;\n\t@q st.relaxed.gpu.global.u64 [%1], %2;\n\t}"
+                 ::"r"((uint32_t)p), "l"(ptr), "l"(v));
+}
+static __device__ __forceinline__ void st_volatile_shared_u64_if(bool p, uint32_t addr, uint64_t v) {
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %0, 0;\n\t@q st.volatile.shared.u64 [%1], %2;\n\t}"
+                 ::"r"((uint32_t)p), "r"(addr), "l"(v));
+}
+
 static __device__ __forceinline__ int ld_acquire_shared(uint32_t addr) {
     int v;
     asm volatile("ld.acquire.cta.shared.s32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");

@@ -109,6 +109,7 @@ __global__ void __launch_bounds__(256, 1) k_pair_bp(const PairArgs P) {
     const uint32_t prod_cols = sbase + lay.ctrl, prod_src = prod_cols + 4, cons0 = prod_cols + 8;
     uint64_t *rings = reinterpret_cast<uint64_t *>(smem + lay.rings);
     uint64_t *ring_out = rings + (size_t)w * kRing;                       // read by warp w+1
+    const uint32_t ring_out_s = (uint32_t)__cvta_generic_to_shared(ring_out);
     const uint64_t *ring_in = rings + (size_t)(w > 0 ? w - 1 : 0) * kRing;  // written by warp w-1
     volatile int *cons = reinterpret_cast<volatile int *>(smem + lay.ctrl + 8);
     uint32_t *pm = reinterpret_cast<uint32_t *>(smem + (size_t)(w < W ? w : 0) * kTableBytes);
@@ -353,16 +354,17 @@ __global__ void __launch_bounds__(256, 1) k_pair_bp(const PairArgs P) {
                         Mcur[jj] = Mnext[jj];
                         onext[jj] = onext2[jj];
                     }
-                    if (i == kFlushStep && lane == 31) {
+                    if (i == kFlushStep) {  // lane 31 completes word wq (a predicated store)
                         const int64_t wq = ((ubase + i - kLag) * C) >> 5;
                         if (w + 1 < W) {
                             // on a timeout the error is raised and every later wait
                             // returns at once, so the strip ends with its result void
-                            wait_consumed(cons + w + 1, (int)(wq - kRing + 1), P.err, P.wait_limit_ns);
-                            reinterpret_cast<volatile uint64_t *>(ring_out)[wq % kRing] =
-                                ((uint64_t)(uint32_t)(wq + ring_tag0) << 32) | cw;
+                            if (lane == 31)
+                                wait_consumed(cons + w + 1, (int)(wq - kRing + 1), P.err, P.wait_limit_ns);
+                            st_volatile_shared_u64_if(lane == 31, ring_out_s + (uint32_t)((wq % kRing) * 8),
+                                                      ((uint64_t)(uint32_t)(wq + ring_tag0) << 32) | cw);
                         } else {
-                            st_relaxed_u64(dst_row + wq, ((uint64_t)P.epoch << 32) | cw);
+                            st_relaxed_u64_if(lane == 31, dst_row + wq, ((uint64_t)P.epoch << 32) | cw);
                         }
                     }
                 }
@@ -396,17 +398,16 @@ __global__ void __launch_bounds__(256, 1) k_pair_bp(const PairArgs P) {
                     const uint32_t recv = __shfl_up_sync(kFull, cw, 1);
                     cin_cur = cin_nxt;
                     cin_nxt = recv;
-                    if (lane == 31 && act && (i == kFlushStep || q == nch - 1)) {
+                    const bool fl = lane == 31 && act && (i == kFlushStep || q == nch - 1);
+                    if (__any_sync(kFull, fl)) {
                         const int64_t wq = (q * C) >> 5;
                         const uint32_t gw = cw << ((32 - C - ((q * C) & 31)) & 31);
                         if (w + 1 < W) {
-                            // on a timeout the error is raised and every later wait
-                            // returns at once, so the strip ends with its result void
-                            wait_consumed(cons + w + 1, (int)(wq - kRing + 1), P.err, P.wait_limit_ns);
-                            reinterpret_cast<volatile uint64_t *>(ring_out)[wq % kRing] =
-                                ((uint64_t)(uint32_t)(wq + ring_tag0) << 32) | gw;
+                            if (fl) wait_consumed(cons + w + 1, (int)(wq - kRing + 1), P.err, P.wait_limit_ns);
+                            st_volatile_shared_u64_if(fl, ring_out_s + (uint32_t)(((wq % kRing) & (kRing - 1)) * 8),
+                                                      ((uint64_t)(uint32_t)(wq + ring_tag0) << 32) | gw);
                         } else {
-                            st_relaxed_u64(dst_row + wq, ((uint64_t)P.epoch << 32) | gw);
+                            st_relaxed_u64_if(fl, dst_row + (fl ? wq : 0), ((uint64_t)P.epoch << 32) | gw);
                         }
                     }
                 }
