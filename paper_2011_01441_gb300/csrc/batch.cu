@@ -91,8 +91,10 @@ struct BatchArgs {
 
 constexpr int kBatchSrcRing = 8;
 constexpr int kBatchSrcAhead = 4;
-// column offsets through a shared ring of 32-column words, copied kColAhead
-// words ahead (lane 31 trails lane 0 by at most 31*8/32 + 1 = 9 words)
+// Column offsets reach the warp through a shared ring of 32-column words,
+// copied kColAhead words ahead (lane 31 trails lane 0 by at most 31*8/32 + 1
+// = 9 words); two mirror slots after the ring repeat slots 0 and 1, so a
+// lane's window of the next 32 + 2C columns never wraps.
 constexpr int kColRing = 32;
 constexpr int kColAhead = 8;
 
@@ -100,17 +102,17 @@ template <int C>
 __global__ void __launch_bounds__(32) k_batch(const BatchArgs P) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ __align__(16) uint64_t s_src[2 * kBatchSrcRing];
-    __shared__ __align__(16) uint32_t s_cols[kColRing * 32];
+    __shared__ __align__(16) uint32_t s_cols[(kColRing + 2) * 32];
     const int lane = threadIdx.x & 31;
     uint32_t *pm = reinterpret_cast<uint32_t *>(smem);
     const uint32_t pm_lane = (uint32_t)__cvta_generic_to_shared(pm + lane);
     const uint32_t col_ring = (uint32_t)__cvta_generic_to_shared(s_cols);
     const uint32_t src_ring = (uint32_t)__cvta_generic_to_shared(s_src);
     for (int c = 0; c < P.table_rows; ++c) pm[c * 32 + lane] = 0u;
+    for (int i = lane; i < (kColRing + 2) * 32; i += 32) s_cols[i] = 0u;  // valid offsets from the start
     const uint32_t epoch = *P.epoch_dev;
 
     constexpr int K = 32 / C;
-    constexpr uint32_t cmask = (C == 32) ? kFull : ((1u << C) - 1u);
     constexpr int kFlushStep = 30 % K;  // lane 31 trails lane 0 by 31 chunks
 
     for (;;) {
@@ -146,16 +148,23 @@ __global__ void __launch_bounds__(32) k_batch(const BatchArgs P) {
             }
         }
         if (badsym) atomicCAS(P.err, 0, kEinval);
-        uint32_t Sv = kK31, Yv = 0;  // zero first column: no vertical steps
+        uint32_t V = 0xffffffffu;  // zero first column: no vertical steps; bit 31 held at 1
         __syncwarp();
 
         const int64_t nch = (S + C - 1) / C;
         const int last_valid = (int)(S - (nch - 1) * C);
+        const int64_t nch_full = (last_valid == C) ? nch : nch - 1;
         const int64_t nwords = (S + 31) >> 5;
         const int64_t npairs = (nwords + 1) >> 1;
         const int64_t nouter = (nch + 31 + K - 1) / K;
+        const int64_t u_fast0 = (31 + K - 1) / K;  // first word with every lane on a full chunk
+        const int64_t u_fast1 = nch_full / K;      // exclusive
         const bool in_global = (J.flags & kInGlobal) != 0;
+        const bool out_global = (J.flags & kOutGlobal) != 0;
         const uint64_t *src_row = P.hbuf + J.hin;
+        uint64_t *dst_row = P.hbuf + J.hout;
+        uint32_t *bout = P.bbits + (J.bword >= 0 ? J.bword : 0);
+        const bool keep_bits = !out_global && J.bword >= 0;
         auto issue_pair = [&](int64_t pr) {
             if (pr < npairs) {
                 const uint32_t dst = src_ring + (uint32_t)((pr % kBatchSrcRing) * 16);
@@ -167,24 +176,29 @@ __global__ void __launch_bounds__(32) k_batch(const BatchArgs P) {
         if (in_global && lane == 0)
             for (int d = 0; d < kBatchSrcAhead; ++d) issue_pair(d);
 
-        uint32_t cw_last = 0, gw = 0, total = 0;
+        uint32_t cw = 0;      // this lane's carry-outs, newest in bit 0 (never reset)
+        uint32_t sr = 0;      // carry-ins, next one in bit 31
+        uint32_t total = 0;   // lane 31 of a final segment: set bits of the bottom row
         bool ok = true;
+        // lanes 0..7 copy one 32-column word (16 bytes each); lanes 8..15 the
+        // mirror copy when the word lands in slot 0 or 1
         auto issue_cols = [&](int64_t wd) {
-            if (lane < 8 && wd < nwords) {
-                const int64_t col = wd * 32 + lane * 4;
+            const int slot = (int)(wd % kColRing);
+            const int part = lane & 7;
+            const bool mine = wd < nwords && (lane < 8 || (lane < 16 && slot < 2));
+            if (mine) {
+                const int64_t col = wd * 32 + part * 4;
                 const int64_t rem = S - col;
                 const int bytes = rem >= 4 ? 16 : (rem > 0 ? (int)rem * 4 : 0);
                 const uint32_t *src = boff + (bytes > 0 ? col : 0);
-                const uint32_t dst = col_ring + (uint32_t)(((wd % kColRing) * 32 + lane * 4) * 4);
+                const int dslot = lane < 8 ? slot : kColRing + slot;
+                const uint32_t dst = col_ring + (uint32_t)((dslot * 32 + part * 4) * 4);
                 asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes)
                              : "memory");
             }
             asm volatile("cp.async.commit_group;" ::: "memory");
         };
-        auto offs_of = [&](int64_t q, uint32_t (&o)[C]) {
-            const int64_t col = q * C;
-            const uint32_t addr = col_ring + (uint32_t)(((((col >> 5) % kColRing) + kColRing) % kColRing) * 128 +
-                                                        (col & 31) * 4);
+        auto offs_at = [&](uint32_t addr, uint32_t (&o)[C]) {
             if constexpr (C == 2) {
                 uint32_t x, y;
                 asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(x), "=r"(y) : "r"(addr));
@@ -221,53 +235,69 @@ __global__ void __launch_bounds__(32) k_batch(const BatchArgs P) {
                 if ((uint32_t)(v >> 32) != epoch) v = poll_global_lane(src_row + u, epoch, P.err, P.wait_limit_ns, lok);
                 srcw = (uint32_t)v;
             }
-            if (!__all_sync(kFull, lok)) {
+            if (in_global && !__all_sync(kFull, lok)) {
                 ok = false;
                 break;
             }
+            if (lane == 0) sr = srcw;
             const int64_t ubase = u * K;
-            uint32_t ocur[C], onext[C];
-            offs_of(ubase - lane, ocur);
+            // this lane's column of step 0 (lane k trails lane 0 by k chunks) in the ring
+            const int64_t c0 = u * 32 - (int64_t)C * lane;
+            const uint32_t cbase = col_ring + (uint32_t)(((c0 >> 5) & (kColRing - 1)) * 128) + (uint32_t)((c0 & 31) * 4);
+            if (u >= u_fast0 && u < u_fast1) {
+                // ---------- steady state: every lane on a full chunk ----------
+                uint32_t ocur[C], onext[C];
+                offs_at(cbase, ocur);
 #pragma unroll
-            for (int i = 0; i < K; ++i) {
-                const int64_t q = ubase + i - lane;
-                if (i + 1 < K) offs_of(q + 1, onext);
-                const uint32_t up = __shfl_up_sync(kFull, cw_last, 1);
-                uint32_t sr = (lane == 0) ? (srcw << (i * C)) : (up << (32 - C));
-                uint32_t cw = 0;
-                const bool act = (q >= 0) && (q < nch);
-                if (act) {
-                    if (q == nch - 1 && last_valid < C) {
+                for (int i = 0; i < K; ++i) {
+                    if (i + 1 < K) offs_at(cbase + (uint32_t)((i + 1) * C * 4), onext);
+                    const uint32_t up = __shfl_up_sync(kFull, cw, 1);
+                    if (lane != 0) sr = up << (32 - C);
 #pragma unroll
-                        for (int jj = 0; jj < C; ++jj) {
-                            if (jj < last_valid) {
-                                const uint32_t M = lds_u32(pm_lane + ocur[jj]);
-                                column31(Sv, Yv, sr, cw, M);
-                            }
-                        }
-                        cw <<= (C - last_valid);
-                    } else {
+                    for (int jj = 0; jj < C; ++jj) column31v(V, sr, cw, lds_u32(pm_lane + ocur[jj]));
 #pragma unroll
-                        for (int jj = 0; jj < C; ++jj) {
-                            const uint32_t M = lds_u32(pm_lane + ocur[jj]);
-                            column31(Sv, Yv, sr, cw, M);
+                    for (int jj = 0; jj < C; ++jj) ocur[jj] = onext[jj];
+                    if (i == kFlushStep) {  // lane 31 completes word wq
+                        const int64_t wq = ((ubase + i - 31) * C) >> 5;
+                        if (out_global) {
+                            st_relaxed_u64_if(lane == 31, dst_row + wq, ((uint64_t)epoch << 32) | cw);
+                        } else if (lane == 31) {
+                            total += __popc(cw);
+                            if (keep_bits) bout[wq] = cw;
                         }
                     }
                 }
+            } else {
+                // ---------- fill / drain: per-lane activity ----------
 #pragma unroll
-                for (int jj = 0; jj < C; ++jj) ocur[jj] = onext[jj];
-                cw_last = cw;
-                if (lane == 31 && act) {
-                    gw |= cw << (32 - C - ((q * C) & 31));
-                    if (i == kFlushStep || q == nch - 1) {
-                        const int64_t wq = (q * C) >> 5;
-                        if (J.flags & kOutGlobal) {
-                            st_relaxed_u64(P.hbuf + J.hout + wq, ((uint64_t)epoch << 32) | gw);
+                for (int i = 0; i < K; ++i) {
+                    const int64_t q = ubase + i - lane;
+                    const uint32_t up = __shfl_up_sync(kFull, cw, 1);
+                    const bool act = (q >= 0) && (q < nch);
+                    uint32_t oq[C];
+                    offs_at(cbase + (uint32_t)(i * C * 4), oq);
+                    if (act) {
+                        if (lane != 0) sr = up << (32 - C);
+                        if (q == nch - 1 && last_valid < C) {
+#pragma unroll
+                            for (int jj = 0; jj < C; ++jj)
+                                if (jj < last_valid) column31v(V, sr, cw, lds_u32(pm_lane + oq[jj]));
+                            cw <<= (C - last_valid);  // keep the chunk MSB-first
                         } else {
-                            total += __popc(gw);
-                            if (J.bword >= 0) P.bbits[J.bword + wq] = gw;
+#pragma unroll
+                            for (int jj = 0; jj < C; ++jj) column31v(V, sr, cw, lds_u32(pm_lane + oq[jj]));
                         }
-                        gw = 0;
+                    }
+                    const bool fl = lane == 31 && act && (i == kFlushStep || q == nch - 1);
+                    if (__any_sync(kFull, fl)) {
+                        const int64_t wq = (q * C) >> 5;
+                        const uint32_t gw = cw << ((32 - C - ((q * C) & 31)) & 31);
+                        if (out_global) {
+                            st_relaxed_u64_if(fl, dst_row + (fl ? wq : 0), ((uint64_t)epoch << 32) | gw);
+                        } else if (fl) {
+                            total += __popc(gw);
+                            if (keep_bits) bout[wq] = gw;
+                        }
                     }
                 }
             }
@@ -276,7 +306,7 @@ __global__ void __launch_bounds__(32) k_batch(const BatchArgs P) {
         __syncwarp();
 
         if (ok && lane == 31 && (J.flags & kFinal)) P.len[J.pair] = (int32_t)total;
-        if (ok && J.rword >= 0 && nreal > 0) P.rbits[J.rword + lane] = ~(Sv | Yv) & realmask;
+        if (ok && J.rword >= 0 && nreal > 0) P.rbits[J.rword + lane] = ~V & realmask;
 #pragma unroll
         for (int r = 0; r < kLaneRows; ++r) {
             if (r < nreal) {

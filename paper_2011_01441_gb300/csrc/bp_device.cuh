@@ -167,6 +167,23 @@ static __device__ __forceinline__ void st_volatile_shared_u64_if(bool p, uint32_
                  ::"r"((uint32_t)p), "r"(addr), "l"(v));
 }
 
+// The column on V itself (bit 31 held at 1, rows in bits 0..30): two LOP3
+// and three adds, the fewest ALU issue slots of the forms here (the single
+// pair, bound by one lane's dependency chain, uses column31c instead).
+//   CC = top bit of sr; X = V & M; A = V + X + CC, CC = carry out;
+//   cw = 2 cw + CC; V' = A | (V & ~M)
+static __device__ __forceinline__ void column31v(uint32_t &V, uint32_t &sr, uint32_t &cw, uint32_t M) {
+    asm("{\n\t.reg .u32 x, a;\n\t"
+        "add.cc.u32 %0, %0, %0;\n\t"
+        "and.b32 x, %1, %3;\n\t"
+        "addc.cc.u32 a, %1, x;\n\t"
+        "addc.u32 %2, %2, %2;\n\t"
+        "lop3.b32 %1, a, %1, %3, 0xF4;\n\t"
+        "}"
+        : "+r"(sr), "+r"(V), "+r"(cw)
+        : "r"(M));
+}
+
 static __device__ __forceinline__ int ld_acquire_shared(uint32_t addr) {
     int v;
     asm volatile("ld.acquire.cta.shared.s32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
