@@ -345,6 +345,12 @@ def run_gpu(args):
     ctx.close()
 
 
+def _chunks_by_class(packed):
+    """Chunk width per size class of the streamed side, as the batch ran."""
+    names = ("S<256", "S<1024", "S<4096", "S>=4096")
+    return {nm: (int(packed) >> (4 * k)) & 15 for k, nm in enumerate(names)}
+
+
 def run_batch_bench(args):
     """The 4096-pair batch through paco_lcs_batch (one graph replay per step)
     against the single-pair path called once per pair."""
@@ -394,7 +400,7 @@ def run_batch_bench(args):
             "warmup": args.warmup, "ms_per_step": sum(ms) / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": bt.name + " (seed 4)", "pairs": bt.npairs, "cells": cells,
-                       "engine": "batch graph, warp jobs", "alphabet": 4, "chunk": P.paco_last_batch_chunk(ctx) if hasattr(P, "paco_last_batch_chunk") else None,
+                       "engine": "batch graph, warp jobs", "alphabet": 4, "chunk_by_class": _chunks_by_class(ctx.get_option(P.OPT_BATCH_CHUNKS)),
                        "l2": "flushed between timed steps"},
             "plain_one_pair_per_launch": None if args.no_plain else
             {"value": cells / plain_s / 1e9, "unit": "GCUPS", "seconds": plain_s},

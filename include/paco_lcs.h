@@ -102,6 +102,10 @@ enum paco_option {
                                    256); a smaller alphabet shrinks the per-warp match
                                    table and raises occupancy.  A symbol outside it never
                                    matches and the call reports PACO_EINVAL */
+    PACO_OPT_BATCH_CHUNKS = 8,  /* read only: chunk widths the last paco_lcs_batch call ran
+                                   with, one per size class of the streamed side
+                                   (< 256, < 1024, < 4096, >= 4096 columns), 4 bits each,
+                                   smallest class in the low bits */
     PACO_OPT_TEST_STALL = 100   /* tests only: make one strip wait on a flag
                                    nothing sets (exercises the bounded wait) */
 };

@@ -34,6 +34,7 @@ OPT_WAIT_LIMIT_NS = 4
 OPT_ORIENT = 5
 OPT_SCHEDULE = 6
 OPT_ALPHABET = 7
+OPT_BATCH_CHUNKS = 8
 OPT_TEST_STALL = 100
 
 _lib = None

@@ -185,6 +185,7 @@ int paco_ctx_get_option(paco_ctx *ctx, int option, int64_t *value) {
         case PACO_OPT_ORIENT: *value = ctx->opt_orient; return PACO_OK;
         case PACO_OPT_SCHEDULE: *value = ctx->opt_schedule; return PACO_OK;
         case PACO_OPT_ALPHABET: *value = ctx->opt_alphabet; return PACO_OK;
+        case PACO_OPT_BATCH_CHUNKS: *value = ctx->last_batch_chunk; return PACO_OK;
         case PACO_OPT_TEST_STALL: *value = ctx->test_stall; return PACO_OK;
         default: return PACO_EINVAL;
     }

@@ -15,6 +15,7 @@
 #include "paco_internal.hpp"
 
 #include <algorithm>
+#include <array>
 #include <chrono>
 #include <cstdio>
 #include <cstring>
@@ -29,6 +30,11 @@ namespace {
 using namespace dev;
 
 enum : uint32_t { kTransposed = 1u, kInGlobal = 2u, kOutGlobal = 4u, kFinal = 8u };
+// Size classes of the streamed side S (bits 8..9 of SegJob::flags); each
+// class runs with its own autotuned chunk width.
+constexpr int kClassShift = 8;
+constexpr int kClasses = 4;
+inline int size_class(int64_t S) { return S < 256 ? 0 : (S < 1024 ? 1 : (S < 4096 ? 2 : 3)); }
 
 struct SegJob {
     int64_t rows_off;  // first row of the segment in the rows string (cat offset)
@@ -87,6 +93,7 @@ struct BatchArgs {
     long long wait_limit_ns;
     int sigma;       // declared alphabet: symbols are < sigma
     int table_rows;  // rows of the per-warp match table (sigma, plus a zero row when < 256)
+    int cls_chunk[4];  // chunk width of each size class
 };
 
 constexpr int kBatchSrcRing = 8;
@@ -98,32 +105,15 @@ constexpr int kBatchSrcAhead = 4;
 constexpr int kColRing = 32;
 constexpr int kColAhead = 8;
 
+// One warp job (a segment of up to 32 lanes x 31 rows of one pair, all its
+// columns) with chunk width C.  The pipeline ends at the segment's last
+// real lane: that lane hands the bottom row on.
 template <int C>
-__global__ void __launch_bounds__(32) k_batch(const BatchArgs P) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ __align__(16) uint64_t s_src[2 * kBatchSrcRing];
-    __shared__ __align__(16) uint32_t s_cols[(kColRing + 2) * 32];
-    const int lane = threadIdx.x & 31;
-    uint32_t *pm = reinterpret_cast<uint32_t *>(smem);
-    const uint32_t pm_lane = (uint32_t)__cvta_generic_to_shared(pm + lane);
-    const uint32_t col_ring = (uint32_t)__cvta_generic_to_shared(s_cols);
-    const uint32_t src_ring = (uint32_t)__cvta_generic_to_shared(s_src);
-    for (int c = 0; c < P.table_rows; ++c) pm[c * 32 + lane] = 0u;
-    for (int i = lane; i < (kColRing + 2) * 32; i += 32) s_cols[i] = 0u;  // valid offsets from the start
-    const uint32_t epoch = *P.epoch_dev;
-
+static __device__ __forceinline__ void batch_job(const BatchArgs &P, const SegJob &J, const int lane, uint32_t *pm,
+                                                 const uint32_t pm_lane, const uint32_t col_ring,
+                                                 const uint32_t src_ring, const uint32_t epoch) {
     constexpr int K = 32 / C;
-    constexpr int kFlushStep = 30 % K;  // lane 31 trails lane 0 by 31 chunks
-
-    for (;;) {
-        int job = 0;
-        if (lane == 0) {
-            job = atomicAdd(P.ticket, 1);
-            if (ld_relaxed_i32(P.err) != 0) job = (int)P.njobs;
-        }
-        job = __shfl_sync(kFull, job, 0);
-        if (job >= P.njobs) break;
-        const SegJob J = P.jobs[job];
+    {
         const bool tr = (J.flags & kTransposed) != 0;
         const uint8_t *rows = tr ? P.b_cat : P.a_cat;
         const uint32_t *boff = P.coffs + J.cols_off;
@@ -156,8 +146,10 @@ __global__ void __launch_bounds__(32) k_batch(const BatchArgs P) {
         const int64_t nch_full = (last_valid == C) ? nch : nch - 1;
         const int64_t nwords = (S + 31) >> 5;
         const int64_t npairs = (nwords + 1) >> 1;
-        const int64_t nouter = (nch + 31 + K - 1) / K;
-        const int64_t u_fast0 = (31 + K - 1) / K;  // first word with every lane on a full chunk
+        const int last = (J.nrows - 1) / kLaneRows;      // last real lane: the pipeline's end
+        const int flush_i = (last + K - 1) % K;         // step at which it completes a word
+        const int64_t nouter = (nch + last + K - 1) / K;
+        const int64_t u_fast0 = (last + K - 1) / K;  // first word with every real lane on a full chunk
         const int64_t u_fast1 = nch_full / K;      // exclusive
         const bool in_global = (J.flags & kInGlobal) != 0;
         const bool out_global = (J.flags & kOutGlobal) != 0;
@@ -257,11 +249,11 @@ __global__ void __launch_bounds__(32) k_batch(const BatchArgs P) {
                     for (int jj = 0; jj < C; ++jj) column31v(V, sr, cw, lds_u32(pm_lane + ocur[jj]));
 #pragma unroll
                     for (int jj = 0; jj < C; ++jj) ocur[jj] = onext[jj];
-                    if (i == kFlushStep) {  // lane 31 completes word wq
-                        const int64_t wq = ((ubase + i - 31) * C) >> 5;
+                    if (i == flush_i) {  // the last lane completes word wq
+                        const int64_t wq = ((ubase + i - last) * C) >> 5;
                         if (out_global) {
-                            st_relaxed_u64_if(lane == 31, dst_row + wq, ((uint64_t)epoch << 32) | cw);
-                        } else if (lane == 31) {
+                            st_relaxed_u64_if(lane == last, dst_row + wq, ((uint64_t)epoch << 32) | cw);
+                        } else if (lane == last) {
                             total += __popc(cw);
                             if (keep_bits) bout[wq] = cw;
                         }
@@ -288,7 +280,7 @@ __global__ void __launch_bounds__(32) k_batch(const BatchArgs P) {
                             for (int jj = 0; jj < C; ++jj) column31v(V, sr, cw, lds_u32(pm_lane + oq[jj]));
                         }
                     }
-                    const bool fl = lane == 31 && act && (i == kFlushStep || q == nch - 1);
+                    const bool fl = lane == last && act && ((((q + 1) * C) & 31) == 0 || q == nch - 1);
                     if (__any_sync(kFull, fl)) {
                         const int64_t wq = (q * C) >> 5;
                         const uint32_t gw = cw << ((32 - C - ((q * C) & 31)) & 31);
@@ -305,7 +297,7 @@ __global__ void __launch_bounds__(32) k_batch(const BatchArgs P) {
         asm volatile("cp.async.wait_all;" ::: "memory");
         __syncwarp();
 
-        if (ok && lane == 31 && (J.flags & kFinal)) P.len[J.pair] = (int32_t)total;
+        if (ok && lane == last && (J.flags & kFinal)) P.len[J.pair] = (int32_t)total;
         if (ok && J.rword >= 0 && nreal > 0) P.rbits[J.rword + lane] = ~V & realmask;
 #pragma unroll
         for (int r = 0; r < kLaneRows; ++r) {
@@ -315,6 +307,36 @@ __global__ void __launch_bounds__(32) k_batch(const BatchArgs P) {
             }
         }
         __syncwarp();
+    }
+}
+
+__global__ void __launch_bounds__(32) k_batch(const BatchArgs P) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ __align__(16) uint64_t s_src[2 * kBatchSrcRing];
+    __shared__ __align__(16) uint32_t s_cols[(kColRing + 2) * 32];
+    const int lane = threadIdx.x & 31;
+    uint32_t *pm = reinterpret_cast<uint32_t *>(smem);
+    const uint32_t pm_lane = (uint32_t)__cvta_generic_to_shared(pm + lane);
+    const uint32_t col_ring = (uint32_t)__cvta_generic_to_shared(s_cols);
+    const uint32_t src_ring = (uint32_t)__cvta_generic_to_shared(s_src);
+    for (int c = 0; c < P.table_rows; ++c) pm[c * 32 + lane] = 0u;
+    for (int i = lane; i < (kColRing + 2) * 32; i += 32) s_cols[i] = 0u;  // valid offsets from the start
+    const uint32_t epoch = *P.epoch_dev;
+    for (;;) {
+        int job = 0;
+        if (lane == 0) {
+            job = atomicAdd(P.ticket, 1);
+            if (ld_relaxed_i32(P.err) != 0) job = (int)P.njobs;
+        }
+        job = __shfl_sync(kFull, job, 0);
+        if (job >= P.njobs) break;
+        const SegJob J = P.jobs[job];
+        // the chunk width of the job's size class
+        const int cl = (int)((J.flags >> kClassShift) & 3u);  // (no dynamic index into the parameters)
+        const int C = cl == 0 ? P.cls_chunk[0] : (cl == 1 ? P.cls_chunk[1] : (cl == 2 ? P.cls_chunk[2] : P.cls_chunk[3]));
+        if (C == 2) batch_job<2>(P, J, lane, pm, pm_lane, col_ring, src_ring, epoch);
+        else if (C == 4) batch_job<4>(P, J, lane, pm, pm_lane, col_ring, src_ring, epoch);
+        else batch_job<8>(P, J, lane, pm, pm_lane, col_ring, src_ring, epoch);
     }
 }
 
@@ -403,42 +425,23 @@ __global__ void k_batch_prefix(const PrefixJob *pj, const uint32_t *bbits, const
     else if (kr) for (int64_t i = threadIdx.x; i <= J.L; i += blockDim.x) kr[i] = 0;
 }
 
-template <int C>
-cudaError_t launch_batch_c(const BatchArgs &a, int grid, cudaStream_t st) {
+cudaError_t launch_batch(const BatchArgs &a, int grid, cudaStream_t st) {
     const size_t smem = (size_t)a.table_rows * 32 * 4;
-    cudaError_t e = cudaFuncSetAttribute(k_batch<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)(kMaxSigma * 32 * 4));
     if (e != cudaSuccess) return e;
-    k_batch<C><<<grid, 32, smem, st>>>(a);
+    k_batch<<<grid, 32, smem, st>>>(a);
     return cudaGetLastError();
 }
 
-template <int C>
-int batch_occupancy(int table_rows) {
+int occupancy_for(int table_rows) {
     const size_t smem = (size_t)table_rows * 32 * 4;
-    if (cudaFuncSetAttribute(k_batch<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kMaxSigma * 32 * 4)) !=
+    if (cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kMaxSigma * 32 * 4)) !=
         cudaSuccess)
         return 1;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<C>, 32, smem) != cudaSuccess) return 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch, 32, smem) != cudaSuccess) return 1;
     return std::max(1, nb);
-}
-
-cudaError_t launch_batch(int C, const BatchArgs &a, int grid, cudaStream_t st) {
-    switch (C) {
-        case 2: return launch_batch_c<2>(a, grid, st);
-        case 4: return launch_batch_c<4>(a, grid, st);
-        case 8: return launch_batch_c<8>(a, grid, st);
-        default: return cudaErrorInvalidValue;
-    }
-}
-
-int occupancy_for(int C, int table_rows) {
-    switch (C) {
-        case 2: return batch_occupancy<2>(table_rows);
-        case 4: return batch_occupancy<4>(table_rows);
-        default: return batch_occupancy<8>(table_rows);
-    }
 }
 
 int table_rows_for(int sigma) { return sigma >= kMaxSigma ? kMaxSigma : sigma + 1; }
@@ -448,6 +451,7 @@ struct Layout {
     std::vector<PrefixJob> pjobs;
     std::vector<ColJob> cjobs;
     int64_t cwords = 0;
+    int64_t class_jobs[kClasses] = {0, 0, 0, 0};
     int64_t hwords = 0, rwords = 0, bwords = 0;
     int64_t cells = 0;
 };
@@ -509,7 +513,7 @@ void plan_batch(int32_t npairs, const int64_t *a_off, const int64_t *b_off, bool
             J.nrows = (int32_t)std::min(seg_rows, L - j * seg_rows);
             J.S = (int32_t)S;
             J.pair = k;
-            J.flags = tr ? kTransposed : 0u;
+            J.flags = (tr ? kTransposed : 0u) | ((uint32_t)size_class(S) << kClassShift);
             J.hin = 0;
             J.hout = 0;
             if (j > 0) {
@@ -529,6 +533,7 @@ void plan_batch(int32_t npairs, const int64_t *a_off, const int64_t *b_off, bool
             if (J.flags & kFinal) J.bword = pj.bword;
             else J.bword = -1;
             lay.jobs.push_back(J);
+            ++lay.class_jobs[size_class(S)];
         }
         if (want_rows || want_cols) lay.pjobs.push_back(pj);
     }
@@ -555,8 +560,9 @@ struct BatchState {
     // captured graph of the whole batch step
     cudaGraphExec_t exec = nullptr;
     uint64_t exec_key = 0;
-    // autotuned chunk width per layout signature
-    std::map<uint64_t, int> tuned;
+    int64_t class_jobs[4] = {0, 0, 0, 0};
+    // autotuned chunk width of each size class, per layout signature
+    std::map<uint64_t, std::array<int, 4>> tuned;
 };
 
 void batch_release(paco_ctx *ctx) {
@@ -567,7 +573,8 @@ void batch_release(paco_ctx *ctx) {
 namespace {
 
 // Enqueue the whole batch step (no allocation, capturable).
-cudaError_t enqueue_batch(paco_ctx *ctx, BatchState *B, int C, int sigma, const uint8_t *a_cat, int64_t a_len,
+cudaError_t enqueue_batch(paco_ctx *ctx, BatchState *B, const std::array<int, 4> &cls, int sigma,
+                          const uint8_t *a_cat, int64_t a_len,
                           const uint8_t *b_cat, int64_t b_len, int32_t npairs, int32_t *d_len,
                           int32_t *rows_cat, int32_t *cols_cat, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(B->ticket_ptr, 0, sizeof(int), st);
@@ -598,8 +605,9 @@ cudaError_t enqueue_batch(paco_ctx *ctx, BatchState *B, int C, int sigma, const 
         A.wait_limit_ns = ctx->wait_limit_ns;
         A.sigma = sigma;
         A.table_rows = table_rows_for(sigma);
-        const int grid = (int)std::min<int64_t>(B->njobs, (int64_t)ctx->sms * occupancy_for(C, A.table_rows));
-        e = launch_batch(C, A, grid, st);
+        for (int k = 0; k < kClasses; ++k) A.cls_chunk[k] = cls[(size_t)k];
+        const int grid = (int)std::min<int64_t>(B->njobs, (int64_t)ctx->sms * occupancy_for(A.table_rows));
+        e = launch_batch(A, grid, st);
         if (e != cudaSuccess) return e;
     }
     if (B->npjobs > 0 && (rows_cat || cols_cat)) {
@@ -669,6 +677,7 @@ int run_batch(paco_ctx *ctx, BatchState *B, const uint8_t *a_cat, const int64_t 
         B->ncjobs = (int64_t)lay.cjobs.size();
         B->njobs = (int64_t)lay.jobs.size();
         B->npjobs = (int64_t)lay.pjobs.size();
+        for (int k = 0; k < kClasses; ++k) B->class_jobs[k] = lay.class_jobs[k];
         B->layout_key = key;
         if (B->exec) {
             cudaGraphExecDestroy(B->exec);
@@ -677,37 +686,66 @@ int run_batch(paco_ctx *ctx, BatchState *B, const uint8_t *a_cat, const int64_t 
         }
     }
 
-    // chunk width: forced, tuned for this layout, or tuned now
-    int C = force_chunk;
-    if (C == 0 && B != ctx->batch) C = 4;
-    if (C == 0) {
+    // chunk width of each size class: forced, tuned for this layout, or tuned
+    // now by coordinate descent over the classes present (each candidate
+    // timed twice, the second run kept)
+    std::array<int, 4> cls = {4, 4, 4, 4};
+    if (force_chunk) {
+        cls = {force_chunk, force_chunk, force_chunk, force_chunk};
+    } else if (B != ctx->batch) {
+        cls = {2, 4, 8, 8};  // serving micro-batches: untuned defaults by size class
+    } else {
         auto it = B->tuned.find(key);
         if (it != B->tuned.end()) {
-            C = it->second;
+            cls = it->second;
         } else {
-            float best = 1e30f;
-            C = 4;
-            for (int cand : {2, 4, 8}) {
-                float ms_sum = 0.f;
-                for (int rep = 0; rep < 2; ++rep) {
+            // best of three runs per candidate (run-to-run noise is a few percent)
+            auto time_it = [&](const std::array<int, 4> &c, float &ms) -> int {
+                ms = 1e30f;
+                for (int rep = 0; rep < 3; ++rep) {
                     cudaEventRecord(ctx->ev0, st);
-                    cudaError_t e = enqueue_batch(ctx, B, cand, sigma, a_cat, a_len, b_cat, b_len, npairs, d_len,
+                    cudaError_t e = enqueue_batch(ctx, B, c, sigma, a_cat, a_len, b_cat, b_len, npairs, d_len,
                                                   rows_cat, cols_cat, st);
                     cudaEventRecord(ctx->ev1, st);
                     if (e == cudaSuccess) e = cudaEventSynchronize(ctx->ev1);
                     if (e != cudaSuccess) return set_cuda_error(ctx, e, "batch autotune");
-                    float ms = 0.f;
-                    cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
-                    if (rep == 1) ms_sum += ms;
+                    float t = 0.f;
+                    cudaEventElapsedTime(&t, ctx->ev0, ctx->ev1);
+                    if (rep > 0) ms = std::min(ms, t);  // the first run also warms caches
                 }
-                if (ms_sum < best) {
-                    best = ms_sum;
-                    C = cand;
+                return PACO_OK;
+            };
+            // one width for every class first, then each class on its own,
+            // largest class (most of the cells) first
+            float best = 1e30f;
+            for (int cand : {2, 4, 8}) {
+                const std::array<int, 4> trial = {cand, cand, cand, cand};
+                float ms = 0.f;
+                if ((rc = time_it(trial, ms)) != PACO_OK) return rc;
+                if (ms < best) {
+                    best = ms;
+                    cls = trial;
                 }
             }
-            B->tuned[key] = C;
+            for (int k = kClasses - 1; k >= 0; --k) {
+                if (B->class_jobs[k] == 0) continue;
+                const int keep = cls[(size_t)k];
+                for (int cand : {2, 4, 8}) {
+                    if (cand == keep) continue;
+                    std::array<int, 4> trial = cls;
+                    trial[(size_t)k] = cand;
+                    float ms = 0.f;
+                    if ((rc = time_it(trial, ms)) != PACO_OK) return rc;
+                    if (ms < best) {
+                        best = ms;
+                        cls = trial;
+                    }
+                }
+            }
+            B->tuned[key] = cls;
         }
     }
+    const int C = cls[0] | (cls[1] << 4) | (cls[2] << 8) | (cls[3] << 12);
     const uint64_t exec_key = fnv(&C, sizeof(C),
                                   fnv(&a_cat, sizeof(a_cat),
                                       fnv(&b_cat, sizeof(b_cat),
@@ -728,7 +766,7 @@ int run_batch(paco_ctx *ctx, BatchState *B, const uint8_t *a_cat, const int64_t 
             cudaGraph_t g = nullptr;
             if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
             if (e == cudaSuccess) {
-                cudaError_t e2 = enqueue_batch(ctx, B, C, sigma, a_cat, a_len, b_cat, b_len, npairs, d_len, rows_cat,
+                cudaError_t e2 = enqueue_batch(ctx, B, cls, sigma, a_cat, a_len, b_cat, b_len, npairs, d_len, rows_cat,
                                                cols_cat, cap);
                 e = cudaStreamEndCapture(cap, &g);
                 if (e2 != cudaSuccess) e = e2;
@@ -741,7 +779,7 @@ int run_batch(paco_ctx *ctx, BatchState *B, const uint8_t *a_cat, const int64_t 
         }
         e = cudaGraphLaunch(B->exec, st);
     } else {
-        e = enqueue_batch(ctx, B, C, sigma, a_cat, a_len, b_cat, b_len, npairs, d_len, rows_cat, cols_cat, st);
+        e = enqueue_batch(ctx, B, cls, sigma, a_cat, a_len, b_cat, b_len, npairs, d_len, rows_cat, cols_cat, st);
     }
     if (timing) {
         cudaEventRecord(ctx->ev1, st);

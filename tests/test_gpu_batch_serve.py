@@ -94,6 +94,20 @@ def test_batch_boundaries_mixed_sizes(ctx, chunk):
     check_batch(ctx, A, B, boundaries=True, chunk=chunk)
 
 
+def test_batch_size_classes_autotuned(ctx):
+    """Pairs in every size class of the streamed side (< 256, < 1024, < 4096,
+    >= 4096 columns) with per-class autotuned chunk widths: results match the
+    oracle, and every class reports a width of 2, 4 or 8."""
+    A, B = [], []
+    for k, (n, m) in enumerate([(100, 90), (700, 600), (2500, 2000), (5000, 4100), (40, 3000), (4500, 300)] * 3):
+        a = W.symbols(91, k, n, 4)
+        A.append(a)
+        B.append(W.mutate_rate(a, 4, 0.15, 92, k)[:m] if m <= n else W.fit_length(a, m, 4, 93, k))
+    check_batch(ctx, A, B, boundaries=True, chunk=0)
+    packed = ctx.get_option(P.OPT_BATCH_CHUNKS)
+    assert all(((packed >> (4 * k)) & 15) in (2, 4, 8) for k in range(4)), hex(packed)
+
+
 def test_batch_tall_pairs_chain_segments(ctx):
     # pairs taller than one warp (992 rows): segments chain through global memory
     A = [W.symbols(5, k, 5000 + 37 * k, 4) for k in range(6)]
