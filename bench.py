@@ -335,7 +335,7 @@ def run_gpu(args):
                           "note": "one lane streams all S columns; lanes trail by 2 chunks each"},
         "e2e": {"value": e2e_val, "unit": "GCUPS", "h2d_bytes_per_step": n + m,
                 "d2h_bytes_per_step": 4 * (n + 1) + 4 * (m + 1) + 4},
-        "gpu_launches": 9 * args.steps,
+        "gpu_launches": 8 * args.steps,
         "clocks": clk,
         "hbm_peak_gbs_measured": peaks.get("hbm_gbs"),
     }
