@@ -106,6 +106,9 @@ enum paco_option {
                                    with, one per size class of the streamed side
                                    (< 256, < 1024, < 4096, >= 4096 columns), 4 bits each,
                                    smallest class in the low bits */
+    PACO_OPT_WORDS_PER_LANE = 9, /* single pair: 31-row words per lane, 1 or 2 (0 =
+                                   planner); two words give each lane two
+                                   dependency chains and halve the strips */
     PACO_OPT_TEST_STALL = 100   /* tests only: make one strip wait on a flag
                                    nothing sets (exercises the bounded wait) */
 };

@@ -47,16 +47,20 @@ typedef struct paco_pair_plan {
     int32_t chunk;      /* columns per lane hand-off                          */
     int32_t warps;      /* warps per CTA strip                                */
     int32_t nstrips;    /* CTA strips (the p of the balanced row split)       */
+    int32_t words_per_lane; /* 31-row words per lane (1 or 2)                 */
+    int32_t pad;
     int64_t L, S;       /* kernel rows (bit dimension) and streamed columns   */
 } paco_pair_plan;
 
 /* Plan one pair for a device with `sms` multiprocessors.  chunk/warps 0 =
  * planner's choice; orient 0 = bits along the longer string, 1 = along a,
- * 2 = along b; schedule 0 = balanced strips, 1 = uniform strips.
+ * 2 = along b; schedule 0 = balanced strips, 1 = uniform strips;
+ * words_per_lane 0 = planner, 1 or 2 (a lane holds 31 or 62 rows).
  * row0 (capacity cap, may be NULL) receives nstrips+1 strip row offsets.
  * Returns 0 or -1. */
 int paco_plan_pair(int64_t n, int64_t m, int32_t sms, int32_t chunk, int32_t warps, int32_t orient,
-                   int32_t schedule, paco_pair_plan *out, int64_t *row0, int64_t cap);
+                   int32_t schedule, int32_t words_per_lane, paco_pair_plan *out, int64_t *row0,
+                   int64_t cap);
 
 #ifdef __cplusplus
 }

@@ -35,6 +35,7 @@ OPT_ORIENT = 5
 OPT_SCHEDULE = 6
 OPT_ALPHABET = 7
 OPT_BATCH_CHUNKS = 8
+OPT_WORDS_PER_LANE = 9
 OPT_TEST_STALL = 100
 
 _lib = None
@@ -54,7 +55,8 @@ class PacoTile(ctypes.Structure):
 
 class PacoPairPlan(ctypes.Structure):
     _fields_ = [("transpose", ctypes.c_int32), ("chunk", ctypes.c_int32), ("warps", ctypes.c_int32),
-                ("nstrips", ctypes.c_int32), ("L", ctypes.c_int64), ("S", ctypes.c_int64)]
+                ("nstrips", ctypes.c_int32), ("words_per_lane", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("L", ctypes.c_int64), ("S", ctypes.c_int64)]
 
 
 class PacoServeStats(ctypes.Structure):
@@ -92,7 +94,7 @@ def load():
         "paco_last_kernel_ms": ([P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_char_p)], INT),
         "paco_plan_partition": ([I64, I64, I32, I64, P, I64, ctypes.POINTER(I64)], INT),
         "paco_plan_partition_deps": ([I64, I64, I32, I64, P, P, I64, ctypes.POINTER(I64)], INT),
-        "paco_plan_pair": ([I64, I64, I32, I32, I32, I32, I32, ctypes.POINTER(PacoPairPlan), P, I64], INT),
+        "paco_plan_pair": ([I64, I64, I32, I32, I32, I32, I32, I32, ctypes.POINTER(PacoPairPlan), P, I64], INT),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -345,12 +347,12 @@ def paco_plan_partition_deps(n: int, m: int, p: int, base: int):
     return off, idx[:nidx.value]
 
 
-def paco_plan_pair(n: int, m: int, sms: int, chunk=0, warps=0, orient=0, schedule=0):
+def paco_plan_pair(n: int, m: int, sms: int, chunk=0, warps=0, orient=0, schedule=0, words_per_lane=0):
     import numpy as np
     pl = PacoPairPlan()
     rows = np.zeros(1 << 16, dtype=np.int64)
-    _check(load().paco_plan_pair(n, m, sms, chunk, warps, orient, schedule, ctypes.byref(pl),
+    _check(load().paco_plan_pair(n, m, sms, chunk, warps, orient, schedule, words_per_lane, ctypes.byref(pl),
                                  rows.ctypes.data_as(ctypes.c_void_p), rows.size))
-    d = {k: getattr(pl, k) for k, _ in PacoPairPlan._fields_}
+    d = {k: getattr(pl, k) for k, _ in PacoPairPlan._fields_ if k != "pad"}
     d["row0"] = rows[:pl.nstrips + 1].copy()
     return d

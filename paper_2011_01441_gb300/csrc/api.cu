@@ -147,7 +147,7 @@ int paco_ctx_set_option(paco_ctx *ctx, int option, int64_t value) {
             ctx->opt_chunk = (int)value;
             return PACO_OK;
         case PACO_OPT_WARPS:
-            if (value < 0 || value > pair_max_warps(kMaxSigma)) return PACO_EINVAL;
+            if (value < 0 || value > pair_max_warps(1)) return PACO_EINVAL;
             ctx->opt_warps = (int)value;
             return PACO_OK;
         case PACO_OPT_WAIT_LIMIT_NS:
@@ -165,6 +165,10 @@ int paco_ctx_set_option(paco_ctx *ctx, int option, int64_t value) {
         case PACO_OPT_ALPHABET:
             if (value < 1 || value > 256) return PACO_EINVAL;
             ctx->opt_alphabet = (int)value;
+            return PACO_OK;
+        case PACO_OPT_WORDS_PER_LANE:
+            if (value < 0 || value > 2) return PACO_EINVAL;
+            ctx->opt_wpl = (int)value;
             return PACO_OK;
         case PACO_OPT_TEST_STALL:
             if (value < -1 || value > 0x7fffffff) return PACO_EINVAL;
@@ -185,6 +189,7 @@ int paco_ctx_get_option(paco_ctx *ctx, int option, int64_t *value) {
         case PACO_OPT_ORIENT: *value = ctx->opt_orient; return PACO_OK;
         case PACO_OPT_SCHEDULE: *value = ctx->opt_schedule; return PACO_OK;
         case PACO_OPT_ALPHABET: *value = ctx->opt_alphabet; return PACO_OK;
+        case PACO_OPT_WORDS_PER_LANE: *value = ctx->opt_wpl; return PACO_OK;
         case PACO_OPT_BATCH_CHUNKS: *value = ctx->last_batch_chunk; return PACO_OK;
         case PACO_OPT_TEST_STALL: *value = ctx->test_stall; return PACO_OK;
         default: return PACO_EINVAL;

@@ -39,7 +39,7 @@ struct paco_ctx {
     // staging for the host-buffer entry point
     DevBuf h_a, h_b, h_top, h_left, h_row, h_col, h_len;
     uint32_t epoch = 0;
-    int opt_engine = 0, opt_chunk = 0, opt_warps = 0, opt_orient = 0, opt_schedule = 0;
+    int opt_engine = 0, opt_chunk = 0, opt_warps = 0, opt_orient = 0, opt_schedule = 0, opt_wpl = 0;
     int test_stall = -1;
     int opt_alphabet = 256;
     long long wait_limit_ns = 2000000000LL;

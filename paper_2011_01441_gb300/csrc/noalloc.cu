@@ -88,12 +88,12 @@ extern "C" int paco_lcs_boundaries_static(const uint8_t *a, int64_t n, const uin
     }
 
     PairPlanOptions o;
-    o.max_warps = pair_max_warps(kMaxSigma);
+    o.max_warps = pair_max_warps(1);
     PairPlan pl;
     if (!plan_pair(n, m, sms, o, pl)) return PACO_EINVAL;
-    o.resident = sms * std::max(1, pair_occupancy(pl.C, pl.W));
+    o.resident = sms * std::max(1, pair_occupancy(pl.C, pl.W, pl.wpl));
     if (!plan_pair(n, m, sms, o, pl)) return PACO_EINVAL;
-    const int occ = std::max(1, pair_occupancy(pl.C, pl.W));
+    const int occ = std::max(1, pair_occupancy(pl.C, pl.W, pl.wpl));
     const int64_t L = pl.L, S = pl.S;
     const int64_t nwords = (S + 31) / 32, hstride = (nwords + 1) & ~(int64_t)1;
     const int64_t lwords = (L + 31) / 32, rwords = (L + 30) / 31;
@@ -128,7 +128,7 @@ extern "C" int paco_lcs_boundaries_static(const uint8_t *a, int64_t n, const uin
     P.nwords = nwords;
     P.hstride = hstride;
     P.strip_row0 = nullptr;
-    P.granules = (L + 30) / 31;
+    P.granules = (L + 31 * pl.wpl - 1) / (31 * pl.wpl);
     P.nstrips = pl.nstrips;
     P.sigma = kMaxSigma;
     P.left_bits = (const uint32_t *)(scr + off_lbits);
@@ -140,7 +140,7 @@ extern "C" int paco_lcs_boundaries_static(const uint8_t *a, int64_t n, const uin
     P.wait_limit_ns = 2000000000LL;
     P.stall_strip = -1;
     const int grid = std::min(pl.nstrips, sms * occ);
-    e = launch_pair_bp(P, pl.C, pl.W, grid, st);
+    e = launch_pair_bp(P, pl.C, pl.W, pl.wpl, grid, st);
     if (e != cudaSuccess) return PACO_EDEVICE;
     PrefixScratch s1{(int64_t *)(scr + off_sums), nblocks};
     e = launch_bits_prefix(nullptr, hbuf + (size_t)pl.nstrips * hstride, S, 32, nullptr, 0, kbottom, d_len, s1,

@@ -40,7 +40,7 @@ struct PairArgs {
     int64_t nwords;              // ceil(S / 32): words per carry row
     int64_t hstride;             // words between carry rows (nwords rounded up to even)
     const int64_t *strip_row0;   // nstrips+1 row offsets (multiples of 31, last = L), or NULL:
-    int64_t granules;            //   then strip s starts at 31*(s*(granules/nstrips) + min(s, granules%nstrips))
+    int64_t granules;            //   then strip s starts at 31*wpl*(s*(granules/nstrips) + min(s, granules%nstrips))
     int nstrips;
     int sigma;                   // match-table rows (symbols must be < sigma)
     const uint32_t *left_bits;   // L bits: vertical steps of the first column
@@ -54,10 +54,11 @@ struct PairArgs {
 };
 
 // Launch helpers (defined in pair_kernels.cu).
-size_t pair_smem_bytes(int warps, int C);  // dynamic shared memory of one CTA
-int pair_max_warps(int sigma);
-int pair_occupancy(int C, int warps);  // resident CTAs per SM
-cudaError_t launch_pair_bp(const PairArgs &p, int C, int warps, int grid, cudaStream_t st);
+// wpl: 31-row words per lane (1 or 2)
+size_t pair_smem_bytes(int warps, int C, int wpl);  // dynamic shared memory of one CTA
+int pair_max_warps(int wpl);
+int pair_occupancy(int C, int warps, int wpl);  // resident CTAs per SM
+cudaError_t launch_pair_bp(const PairArgs &p, int C, int warps, int wpl, int grid, cudaStream_t st);
 
 // Input boundary (int32, len+1 values) -> step bits (len bits) with checks.
 cudaError_t launch_boundary_bits(const int32_t *v, int64_t len, uint32_t *bits,

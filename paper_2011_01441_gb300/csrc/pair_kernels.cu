@@ -34,36 +34,44 @@ namespace {
 
 using namespace dev;
 
-// Lane skew in chunks: lane k works on chunk t - 2k at step t, so the
-// carry word a lane receives from the lane above (one __shfl_up_sync per
-// step) was produced a full step before it is needed.
-constexpr int kSkew = 2;
+// Lane skew in chunks: with one word per lane, lane k works on chunk t - 2k
+// at step t; with two words (the lower word one chunk behind the upper, fed
+// by its carries in registers) lane k's upper word works on chunk t - 3k.
+// Either way the carry word a lane receives from the lane above (one
+// __shfl_up_sync after each step's columns) was sent two steps before it is
+// needed.
+template <int WPL> __host__ __device__ constexpr int lane_skew() { return WPL == 1 ? 2 : 3; }
+// Chunks the last word of lane 31 trails the first word of lane 0.
+template <int WPL> __host__ __device__ constexpr int lane_lag() { return lane_skew<WPL>() * 31 + (WPL - 1); }
 // Warp 0's input carry words pass through a shared ring of kSrcSlots words.
 constexpr int kSrcSlots = 64;
 // Column-word lag of the oldest word a warp still reads behind the word its
-// lane 0 is on: lane 31 trails lane 0 by kSkew * 31 chunks.
-__host__ __device__ constexpr int col_lag_words(int C) { return (kSkew * 31 * C + 31) / 32 + 1; }
-// Column-offset ring slots (a power of two) for C and W compute warps: the
-// lag of the last warp behind the first, the in-warp lag and some lookahead.
-__host__ __device__ constexpr int col_slots(int C, int W) {
-    const int need = col_lag_words(C) + 4 + (W - 1) * (col_lag_words(C) + 2) + 8;
+// lane 0 is on (the lower word reuses the upper word's offsets).
+__host__ __device__ constexpr int col_lag_words(int C, int WPL) {
+    return ((WPL == 1 ? 2 : 3) * 31 * C + 31) / 32 + 1;
+}
+// Column-offset ring slots (a power of two) for C, W compute warps and WPL
+// words per lane: the lag of the last warp behind the first, the in-warp lag
+// and some lookahead.
+__host__ __device__ constexpr int col_slots(int C, int W, int WPL) {
+    const int need = col_lag_words(C, WPL) + 4 + (W - 1) * (col_lag_words(C, WPL) + 2) + 8;
     int r = 32;
     while (r < need) r <<= 1;
     return r;
 }
 
-// Shared-memory layout of one CTA: W match tables, the column-offset ring
-// (slots + two mirror slots, so a lane's window of the next 32 + 2C columns
-// never wraps), the
-// input ring of warp 0, the rings between consecutive warps, counters.
+// Shared-memory layout of one CTA: W x WPL match tables, the column-offset
+// ring (slots + two mirror slots, so a lane's window of the next 32 + 2C
+// columns never wraps), the input ring of warp 0, the rings between
+// consecutive warps, counters.
 struct PairSmem {
     uint32_t tables, colring, srcring, rings, ctrl, bytes;
 };
-__host__ __device__ inline PairSmem pair_smem_layout(int W, int C) {
+__host__ __device__ inline PairSmem pair_smem_layout(int W, int C, int WPL) {
     PairSmem L;
     L.tables = 0;
-    L.colring = (uint32_t)(W * kTableBytes);
-    L.srcring = L.colring + (uint32_t)(col_slots(C, W) + 2) * 128u;
+    L.colring = (uint32_t)(W * WPL * kTableBytes);
+    L.srcring = L.colring + (uint32_t)(col_slots(C, W, WPL) + 2) * 128u;
     L.rings = L.srcring + (uint32_t)kSrcSlots * 4u;
     L.ctrl = L.rings + (uint32_t)(W * kRing * 8);
     L.bytes = L.ctrl + (uint32_t)(2 + W) * 4u + 16u;
@@ -93,16 +101,24 @@ static __device__ __noinline__ bool wait_inputs(uint32_t prod_cols, uint32_t pro
     return __all_sync(kFull, ok);
 }
 
+// The match words of one chunk: the lane's row bits for each column's symbol.
 template <int C>
+static __device__ __forceinline__ void match_words(uint32_t pm_lane, const uint32_t (&o)[C], uint32_t (&M)[C]) {
+#pragma unroll
+    for (int jj = 0; jj < C; ++jj) M[jj] = lds_u32(pm_lane + o[jj]);
+}
+
+template <int C, int WPL>
 __global__ void __launch_bounds__(256, 1) k_pair_bp(const PairArgs P) {
     static_assert(C == 2 || C == 4 || C == 8, "chunk widths 2, 4 and 8");
+    static_assert(WPL == 1 || WPL == 2, "one or two words per lane");
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_strip;
     const int W = (int)(blockDim.x >> 5) - 1;  // compute warps; warp W produces
     const int w = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    const PairSmem lay = pair_smem_layout(W, C);
-    const int R = col_slots(C, W);
+    const PairSmem lay = pair_smem_layout(W, C, WPL);
+    const int R = col_slots(C, W, WPL);
     const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
     const uint32_t col_ring = sbase + lay.colring;
     const uint32_t src_ring = sbase + lay.srcring;
@@ -112,19 +128,24 @@ __global__ void __launch_bounds__(256, 1) k_pair_bp(const PairArgs P) {
     const uint32_t ring_out_s = (uint32_t)__cvta_generic_to_shared(ring_out);
     const uint64_t *ring_in = rings + (size_t)(w > 0 ? w - 1 : 0) * kRing;  // written by warp w-1
     volatile int *cons = reinterpret_cast<volatile int *>(smem + lay.ctrl + 8);
-    uint32_t *pm = reinterpret_cast<uint32_t *>(smem + (size_t)(w < W ? w : 0) * kTableBytes);
-    const uint32_t pm_lane = (uint32_t)__cvta_generic_to_shared(pm + lane);
+    // table of word x of this warp (x = 0 upper, 1 lower)
+    uint32_t *pm0 = reinterpret_cast<uint32_t *>(smem + (size_t)(w < W ? w * WPL : 0) * kTableBytes);
+    uint32_t *pm1 = pm0 + (WPL == 2 ? kTableBytes / 4 : 0);
+    const uint32_t pm_lane0 = (uint32_t)__cvta_generic_to_shared(pm0 + lane);
+    const uint32_t pm_lane1 = (uint32_t)__cvta_generic_to_shared(pm1 + lane);
 
     if (w < W)
-        for (int c = 0; c < kMaxSigma; ++c) pm[c * 32 + lane] = 0u;
+        for (int c = 0; c < kMaxSigma * WPL; ++c) pm0[c * 32 + lane] = 0u;
     // every ring slot holds a valid table offset from the start
     for (int i = threadIdx.x; i < (R + 2) * 32; i += blockDim.x)
         reinterpret_cast<uint32_t *>(smem + lay.colring)[i] = 0u;
 
-    constexpr int K = 32 / C;                      // steps per 32-column word
-    constexpr int kLag = kSkew * 31;               // chunks lane 31 trails lane 0
-    constexpr int kFlushStep = (kLag - 1) % K;     // step at which lane 31 completes a word
-    constexpr int kLagW = col_lag_words(C);
+    constexpr int K = 32 / C;                       // steps per 32-column word
+    constexpr int kSk = lane_skew<WPL>();
+    constexpr int kLag = lane_lag<WPL>();           // chunks lane 31's last word trails lane 0
+    constexpr int kFlushStep = (kLag - 1) % K;      // step at which lane 31 completes a word
+    constexpr int kLagW = col_lag_words(C, WPL);
+    constexpr int kRowsLane = kLaneRows * WPL;
     const int64_t nch = P.nchunks;
     const int last_valid = (int)(P.S - (nch - 1) * C);
     const int64_t nch_full = (last_valid == C) ? nch : nch - 1;
@@ -229,49 +250,69 @@ __global__ void __launch_bounds__(256, 1) k_pair_bp(const PairArgs P) {
         if (P.strip_row0) {
             row0 = P.strip_row0[s];
             row1 = P.strip_row0[s + 1];
-        } else {  // the balanced split, computed in place
+        } else {  // the balanced split in granules of one lane's rows, computed in place
             const int64_t q = P.granules / P.nstrips, r = P.granules % P.nstrips;
-            row0 = min(P.L, (int64_t)kLaneRows * ((int64_t)s * q + min((int64_t)s, r)));
-            row1 = min(P.L, (int64_t)kLaneRows * ((int64_t)(s + 1) * q + min((int64_t)(s + 1), r)));
+            row0 = min(P.L, (int64_t)kRowsLane * ((int64_t)s * q + min((int64_t)s, r)));
+            row1 = min(P.L, (int64_t)kRowsLane * ((int64_t)(s + 1) * q + min((int64_t)(s + 1), r)));
         }
-        const int64_t rbase = row0 + (int64_t)w * (32 * kLaneRows) + (int64_t)lane * kLaneRows;
-        const int64_t left_rows = row1 - rbase;
-        const int nreal = left_rows <= 0 ? 0 : (left_rows >= kLaneRows ? kLaneRows : (int)left_rows);
-        const uint32_t realmask = (1u << nreal) - 1u;
-
-        // this lane's 31 row symbols -> its column of the match table
-        uint32_t aw[8];
+        const int64_t lbase = row0 + (int64_t)w * (32 * kRowsLane) + (int64_t)lane * kRowsLane;
+        // per word x: first row, real rows, row symbols
+        int64_t rbase[WPL];
+        int nreal[WPL];
+        uint32_t realmask[WPL];
+        uint32_t aw[WPL][8];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) aw[k] = 0;
+        for (int x = 0; x < WPL; ++x) {
+            rbase[x] = lbase + x * kLaneRows;
+            const int64_t left_rows = row1 - rbase[x];
+            nreal[x] = left_rows <= 0 ? 0 : (left_rows >= kLaneRows ? kLaneRows : (int)left_rows);
+            realmask[x] = (1u << nreal[x]) - 1u;
 #pragma unroll
-        for (int r = 0; r < kLaneRows; ++r)
-            if (r < nreal) aw[r >> 2] |= (uint32_t)__ldg(P.a + rbase + r) << ((r & 3) * 8);
+            for (int k = 0; k < 8; ++k) aw[x][k] = 0;
 #pragma unroll
-        for (int r = 0; r < kLaneRows; ++r) {
-            if (r < nreal) {
-                const uint32_t ch = (aw[r >> 2] >> ((r & 3) * 8)) & 0xffu;
-                pm[ch * 32 + lane] |= 1u << r;
+            for (int r = 0; r < kLaneRows; ++r)
+                if (r < nreal[x]) aw[x][r >> 2] |= (uint32_t)__ldg(P.a + rbase[x] + r) << ((r & 3) * 8);
+            uint32_t *pmx = x == 0 ? pm0 : pm1;
+#pragma unroll
+            for (int r = 0; r < kLaneRows; ++r) {
+                if (r < nreal[x]) {
+                    const uint32_t ch = (aw[x][r >> 2] >> ((r & 3) * 8)) & 0xffu;
+                    pmx[ch * 32 + lane] |= 1u << r;
+                }
             }
         }
         // V from the first column's vertical steps (bit set = no step),
         // padding rows 1, bit 31 held at 1
-        uint32_t Sv = 0xffffffffu, Yv = 0;
-        if (nreal > 0) {
+        uint32_t Sv[WPL], Yv[WPL];
+        {
             const int64_t lwords = (P.L + 31) >> 5;
-            const int64_t wi = rbase >> 5;
-            const uint32_t lo = __ldg(P.left_bits + wi);
-            const uint32_t hi = (wi + 1 < lwords) ? __ldg(P.left_bits + wi + 1) : 0u;
-            const uint32_t steps = __funnelshift_r(lo, hi, (uint32_t)(rbase & 31)) & realmask;
-            Sv = ~steps;
+#pragma unroll
+            for (int x = 0; x < WPL; ++x) {
+                Sv[x] = 0xffffffffu;
+                Yv[x] = 0;
+                if (nreal[x] > 0) {
+                    const int64_t wi = rbase[x] >> 5;
+                    const uint32_t lo = __ldg(P.left_bits + wi);
+                    const uint32_t hi = (wi + 1 < lwords) ? __ldg(P.left_bits + wi + 1) : 0u;
+                    const uint32_t steps = __funnelshift_r(lo, hi, (uint32_t)(rbase[x] & 31)) & realmask[x];
+                    Sv[x] = ~steps;
+                }
+            }
         }
         __syncwarp();
 
-        uint32_t cw = 0;        // this lane's carry-outs, newest in bit 0 (never reset)
+        uint32_t cw[WPL], sr[WPL];  // carry-outs (newest in bit 0, never reset); carry-ins (next in bit 31)
+#pragma unroll
+        for (int x = 0; x < WPL; ++x) {
+            cw[x] = 0;
+            sr[x] = 0;
+        }
         uint32_t cin_cur = 0;   // the lane above's carry word for this step (sent two steps ago)
         uint32_t cin_nxt = 0;   // ... and for the next step
-        uint32_t sr = 0;        // carry-ins, next one in bit 31
-        uint32_t Mcur[C];       // steady state: this step's match words
+        uint32_t Mcur[C];       // steady state: the upper word's match words for this step
         uint32_t onext[C];      // steady state: the next step's column offsets
+        uint32_t oprev[C];      // two words: this step's offsets, for the lower word next step
+        uint32_t Mlow[C];       // two words: the lower word's match words for this step
         bool ok = true;
         const uint32_t ring_tag0 = 1;
         for (int64_t u = 0; u < nouter; ++u) {
@@ -301,9 +342,13 @@ __global__ void __launch_bounds__(256, 1) k_pair_bp(const PairArgs P) {
             }
             if (lane == 0) st_release_shared(cons0 + 4u * (uint32_t)w, (int)(u + 1));
             const int64_t ubase = u * K;
-            // this lane's column of step 0 and its place in the ring
-            const int64_t c0 = u * 32 - (int64_t)kSkew * C * lane;
+            // this lane's column of step 0 (upper word) and its place in the ring
+            const int64_t c0 = u * 32 - (int64_t)kSk * C * lane;
             const uint32_t cbase = col_ring + (uint32_t)(((c0 >> 5) & (R - 1)) * 128) + (uint32_t)((c0 & 31) * 4);
+            // the lower word's column of step 0 (one chunk behind) in the ring
+            const int64_t c0l = c0 - C;
+            const uint32_t cbase_l =
+                col_ring + (uint32_t)(((c0l >> 5) & (R - 1)) * 128) + (uint32_t)((c0l & 31) * 4);
             auto offs_at = [&](uint32_t addr, uint32_t (&o)[C]) {
                 if constexpr (C == 2) {
                     uint32_t x, y;
@@ -323,9 +368,9 @@ __global__ void __launch_bounds__(256, 1) k_pair_bp(const PairArgs P) {
                     }
                 }
             };
-            if (lane == 0) sr = srcw;
+            if (lane == 0) sr[0] = srcw;
             if (u >= u_fast0 && u < u_fast1) {
-                // ---------- steady state: all lanes hold full chunks ----------
+                // ---------- steady state: every word of every lane on a full chunk ----------
                 // Software pipeline: offsets two steps ahead, match words one
                 // step ahead, the carry hand-off after the step's columns (its
                 // result is used two steps later), so a warp issuing in order
@@ -333,25 +378,44 @@ __global__ void __launch_bounds__(256, 1) k_pair_bp(const PairArgs P) {
                 if (u == u_fast0) {  // later words: carried over from the step before
                     uint32_t o0[C];
                     offs_at(cbase, o0);
+                    match_words<C>(pm_lane0, o0, Mcur);
+                    if constexpr (WPL == 2) {
+                        uint32_t om[C];
+                        offs_at(cbase_l, om);  // the lower word's chunk: one behind
+                        match_words<C>(pm_lane1, om, Mlow);
 #pragma unroll
-                    for (int jj = 0; jj < C; ++jj) Mcur[jj] = lds_u32(pm_lane + o0[jj]);
+                        for (int jj = 0; jj < C; ++jj) oprev[jj] = o0[jj];
+                    }
                     offs_at(cbase + (uint32_t)(C * 4), onext);
                 }
 #pragma unroll
                 for (int i = 0; i < K; ++i) {
-                    uint32_t onext2[C], Mnext[C];
+                    uint32_t onext2[C], Mnext[C], Mlow_next[C];
                     offs_at(cbase + (uint32_t)((i + 2) * C * 4), onext2);
+                    match_words<C>(pm_lane0, onext, Mnext);
+                    if constexpr (WPL == 2) match_words<C>(pm_lane1, oprev, Mlow_next);
+                    if (lane != 0) sr[0] = cin_cur << (32 - C);
+                    if constexpr (WPL == 2) {
+                        sr[1] = cw[0] << (32 - C);  // the upper word's carries of the step before
 #pragma unroll
-                    for (int jj = 0; jj < C; ++jj) Mnext[jj] = lds_u32(pm_lane + onext[jj]);
-                    if (lane != 0) sr = cin_cur << (32 - C);
+                        for (int jj = 0; jj < C; ++jj) {
+                            column31c(Sv[0], Yv[0], sr[0], cw[0], Mcur[jj]);
+                            column31c(Sv[1], Yv[1], sr[1], cw[1], Mlow[jj]);
+                        }
+                    } else {
 #pragma unroll
-                    for (int jj = 0; jj < C; ++jj) column31c(Sv, Yv, sr, cw, Mcur[jj]);
-                    const uint32_t recv = __shfl_up_sync(kFull, cw, 1);
+                        for (int jj = 0; jj < C; ++jj) column31c(Sv[0], Yv[0], sr[0], cw[0], Mcur[jj]);
+                    }
+                    const uint32_t recv = __shfl_up_sync(kFull, cw[WPL - 1], 1);
                     cin_cur = cin_nxt;
                     cin_nxt = recv;
 #pragma unroll
                     for (int jj = 0; jj < C; ++jj) {
                         Mcur[jj] = Mnext[jj];
+                        if constexpr (WPL == 2) {
+                            Mlow[jj] = Mlow_next[jj];
+                            oprev[jj] = onext[jj];
+                        }
                         onext[jj] = onext2[jj];
                     }
                     if (i == kFlushStep) {  // lane 31 completes word wq (a predicated store)
@@ -362,9 +426,9 @@ __global__ void __launch_bounds__(256, 1) k_pair_bp(const PairArgs P) {
                             if (lane == 31)
                                 wait_consumed(cons + w + 1, (int)(wq - kRing + 1), P.err, P.wait_limit_ns);
                             st_volatile_shared_u64_if(lane == 31, ring_out_s + (uint32_t)((wq % kRing) * 8),
-                                                      ((uint64_t)(uint32_t)(wq + ring_tag0) << 32) | cw);
+                                                      ((uint64_t)(uint32_t)(wq + ring_tag0) << 32) | cw[WPL - 1]);
                         } else {
-                            st_relaxed_u64_if(lane == 31, dst_row + wq, ((uint64_t)P.epoch << 32) | cw);
+                            st_relaxed_u64_if(lane == 31, dst_row + wq, ((uint64_t)P.epoch << 32) | cw[WPL - 1]);
                         }
                     }
                 }
@@ -372,36 +436,55 @@ __global__ void __launch_bounds__(256, 1) k_pair_bp(const PairArgs P) {
                 // ---------- fill / drain: the same windows, per-lane activity ----------
 #pragma unroll
                 for (int i = 0; i < K; ++i) {
-                    const int64_t q = ubase + i - (int64_t)kSkew * lane;
-                    const bool act = (q >= 0) && (q < nch);
+                    const int64_t q = ubase + i - (int64_t)kSk * lane;  // the upper word's chunk
                     uint32_t oq[C];
                     offs_at(cbase + (uint32_t)(i * C * 4), oq);
-                    if (act) {
-                        if (lane != 0) sr = cin_cur << (32 - C);
-                        if (q == nch - 1 && last_valid < C) {
+                    bool last_act = false;
+                    int64_t qlast = q;
+                    if constexpr (WPL == 2) {
+                        // lower word first: its carries are the upper word's of the step before
+                        const int64_t ql = q - 1;
+                        const bool actl = (ql >= 0) && (ql < nch);
+                        uint32_t ol[C];
+                        offs_at(cbase_l + (uint32_t)(i * C * 4), ol);
+                        if (actl) {
+                            sr[1] = cw[0] << (32 - C);
+                            if (ql == nch - 1 && last_valid < C) {
 #pragma unroll
-                            for (int jj = 0; jj < C; ++jj) {
-                                if (jj < last_valid) {
-                                    const uint32_t M = lds_u32(pm_lane + oq[jj]);
-                                    column31c(Sv, Yv, sr, cw, M);
-                                }
-                            }
-                            cw <<= (C - last_valid);  // keep the chunk MSB-first
-                        } else {
+                                for (int jj = 0; jj < C; ++jj)
+                                    if (jj < last_valid) column31c(Sv[1], Yv[1], sr[1], cw[1], lds_u32(pm_lane1 + ol[jj]));
+                                cw[1] <<= (C - last_valid);
+                            } else {
 #pragma unroll
-                            for (int jj = 0; jj < C; ++jj) {
-                                const uint32_t M = lds_u32(pm_lane + oq[jj]);
-                                column31c(Sv, Yv, sr, cw, M);
+                                for (int jj = 0; jj < C; ++jj)
+                                    column31c(Sv[1], Yv[1], sr[1], cw[1], lds_u32(pm_lane1 + ol[jj]));
                             }
                         }
+                        last_act = actl;
+                        qlast = ql;
                     }
-                    const uint32_t recv = __shfl_up_sync(kFull, cw, 1);
+                    const bool act = (q >= 0) && (q < nch);
+                    if (act) {
+                        if (lane != 0) sr[0] = cin_cur << (32 - C);
+                        if (q == nch - 1 && last_valid < C) {
+#pragma unroll
+                            for (int jj = 0; jj < C; ++jj)
+                                if (jj < last_valid) column31c(Sv[0], Yv[0], sr[0], cw[0], lds_u32(pm_lane0 + oq[jj]));
+                            cw[0] <<= (C - last_valid);  // keep the chunk MSB-first
+                        } else {
+#pragma unroll
+                            for (int jj = 0; jj < C; ++jj)
+                                column31c(Sv[0], Yv[0], sr[0], cw[0], lds_u32(pm_lane0 + oq[jj]));
+                        }
+                    }
+                    if constexpr (WPL == 1) last_act = act;
+                    const uint32_t recv = __shfl_up_sync(kFull, cw[WPL - 1], 1);
                     cin_cur = cin_nxt;
                     cin_nxt = recv;
-                    const bool fl = lane == 31 && act && (i == kFlushStep || q == nch - 1);
+                    const bool fl = lane == 31 && last_act && (((qlast + 1) % K) == 0 || qlast == nch - 1);
                     if (__any_sync(kFull, fl)) {
-                        const int64_t wq = (q * C) >> 5;
-                        const uint32_t gw = cw << ((32 - C - ((q * C) & 31)) & 31);
+                        const int64_t wq = (qlast * C) >> 5;
+                        const uint32_t gw = cw[WPL - 1] << ((32 - C - ((qlast * C) & 31)) & 31);
                         if (w + 1 < W) {
                             if (fl) wait_consumed(cons + w + 1, (int)(wq - kRing + 1), P.err, P.wait_limit_ns);
                             st_volatile_shared_u64_if(fl, ring_out_s + (uint32_t)(((wq % kRing) & (kRing - 1)) * 8),
@@ -413,12 +496,16 @@ __global__ void __launch_bounds__(256, 1) k_pair_bp(const PairArgs P) {
                 }
             }
         }
-        if (ok && nreal > 0) P.right_bits[rbase / kLaneRows] = ~(Sv | Yv) & realmask;
 #pragma unroll
-        for (int r = 0; r < kLaneRows; ++r) {
-            if (r < nreal) {
-                const uint32_t ch = (aw[r >> 2] >> ((r & 3) * 8)) & 0xffu;
-                pm[ch * 32 + lane] = 0u;
+        for (int x = 0; x < WPL; ++x) {
+            if (ok && nreal[x] > 0) P.right_bits[rbase[x] / kLaneRows] = ~(Sv[x] | Yv[x]) & realmask[x];
+            uint32_t *pmx = x == 0 ? pm0 : pm1;
+#pragma unroll
+            for (int r = 0; r < kLaneRows; ++r) {
+                if (r < nreal[x]) {
+                    const uint32_t ch = (aw[x][r >> 2] >> ((r & 3) * 8)) & 0xffu;
+                    pmx[ch * 32 + lane] = 0u;
+                }
             }
         }
     }
@@ -655,50 +742,67 @@ __global__ void k_int_peak(int op, int iters, uint32_t *sink) {
 
 }  // namespace
 
-size_t pair_smem_bytes(int warps, int C) { return pair_smem_layout(warps, C).bytes; }
+size_t pair_smem_bytes(int warps, int C, int wpl) { return pair_smem_layout(warps, C, wpl).bytes; }
 
-int pair_max_warps(int /*sigma*/) {
+int pair_max_warps(int wpl) {
     int w = 1;  // the widest chunk (largest column ring) bounds every configuration
-    while (w < 7 && pair_smem_bytes(w + 1, 8) <= 227 * 1024 - 64) ++w;
+    while (w < 7 && pair_smem_bytes(w + 1, 8, wpl) <= 227 * 1024 - 64) ++w;
     return w;
 }
 
-template <int C>
-static cudaError_t launch_c(const PairArgs &p, int warps, int grid, cudaStream_t st) {
-    const size_t smem = pair_smem_bytes(warps, C);
-    cudaError_t e = cudaFuncSetAttribute(k_pair_bp<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+template <int C, int WPL>
+static cudaError_t launch_cw(const PairArgs &p, int warps, int grid, cudaStream_t st) {
+    const size_t smem = pair_smem_bytes(warps, C, WPL);
+    cudaError_t e = cudaFuncSetAttribute(k_pair_bp<C, WPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    k_pair_bp<C><<<grid, (warps + 1) * 32, smem, st>>>(p);  // + the producer warp
+    k_pair_bp<C, WPL><<<grid, (warps + 1) * 32, smem, st>>>(p);  // + the producer warp
     return cudaGetLastError();
 }
 
-template <int C>
-static int occ_c(int warps) {
-    const size_t smem = pair_smem_bytes(warps, C);
-    if (cudaFuncSetAttribute(k_pair_bp<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+template <int C, int WPL>
+static int occ_cw(int warps) {
+    const size_t smem = pair_smem_bytes(warps, C, WPL);
+    if (cudaFuncSetAttribute(k_pair_bp<C, WPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return 0;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pair_bp<C>, (warps + 1) * 32, smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pair_bp<C, WPL>, (warps + 1) * 32, smem) !=
+        cudaSuccess)
         return 0;
     return nb;
 }
 
-int pair_occupancy(int C, int warps) {
+int pair_occupancy(int C, int warps, int wpl) {
+    if (wpl == 2) {
+        switch (C) {
+            case 2: return occ_cw<2, 2>(warps);
+            case 4: return occ_cw<4, 2>(warps);
+            case 8: return occ_cw<8, 2>(warps);
+            default: return 0;
+        }
+    }
     switch (C) {
-        case 2: return occ_c<2>(warps);
-        case 4: return occ_c<4>(warps);
-        case 8: return occ_c<8>(warps);
+        case 2: return occ_cw<2, 1>(warps);
+        case 4: return occ_cw<4, 1>(warps);
+        case 8: return occ_cw<8, 1>(warps);
         default: return 0;
     }
 }
 
-cudaError_t launch_pair_bp(const PairArgs &p, int C, int warps, int grid, cudaStream_t st) {
+cudaError_t launch_pair_bp(const PairArgs &p, int C, int warps, int wpl, int grid, cudaStream_t st) {
+    if (wpl == 2) {
+        switch (C) {
+            case 2: return launch_cw<2, 2>(p, warps, grid, st);
+            case 4: return launch_cw<4, 2>(p, warps, grid, st);
+            case 8: return launch_cw<8, 2>(p, warps, grid, st);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     switch (C) {
-        case 2: return launch_c<2>(p, warps, grid, st);
-        case 4: return launch_c<4>(p, warps, grid, st);
-        case 8: return launch_c<8>(p, warps, grid, st);
+        case 2: return launch_cw<2, 1>(p, warps, grid, st);
+        case 4: return launch_cw<4, 1>(p, warps, grid, st);
+        case 8: return launch_cw<8, 1>(p, warps, grid, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -11,7 +11,7 @@ namespace paco {
 
 const CachedPairPlan *get_pair_plan(paco_ctx *ctx, int64_t n, int64_t m, int *rc) {
     const auto key = std::make_tuple(n, m, ctx->opt_chunk, ctx->opt_warps, ctx->opt_orient,
-                                     ctx->opt_schedule);
+                                     ctx->opt_schedule * 4 + ctx->opt_wpl);
     auto it = ctx->plans.find(key);
     if (it != ctx->plans.end()) {
         *rc = PACO_OK;
@@ -28,20 +28,21 @@ const CachedPairPlan *get_pair_plan(paco_ctx *ctx, int64_t n, int64_t m, int *rc
     o.warps = ctx->opt_warps;
     o.orient = ctx->opt_orient;
     o.schedule = ctx->opt_schedule;
-    o.max_warps = pair_max_warps(kMaxSigma);
+    o.wpl = ctx->opt_wpl;
+    o.max_warps = pair_max_warps(o.wpl == 2 ? 2 : 1);
     auto cp = std::make_unique<CachedPairPlan>();
     // resident CTAs for the chosen chunk width; plan once to learn C and W
     if (!plan_pair(n, m, ctx->sms, o, cp->plan)) {
         *rc = PACO_EINVAL;
         return nullptr;
     }
-    o.resident = ctx->sms * std::max(1, pair_occupancy(cp->plan.C, cp->plan.W));
+    o.resident = ctx->sms * std::max(1, pair_occupancy(cp->plan.C, cp->plan.W, cp->plan.wpl));
     if (!plan_pair(n, m, ctx->sms, o, cp->plan)) {
         *rc = PACO_EINVAL;
         return nullptr;
     }
     // the planner may have raised W; the grid must fit what is resident
-    const int occ = std::max(1, pair_occupancy(cp->plan.C, cp->plan.W));
+    const int occ = std::max(1, pair_occupancy(cp->plan.C, cp->plan.W, cp->plan.wpl));
     cp->plan.grid = std::min(cp->plan.nstrips, ctx->sms * occ);
     const size_t bytes = cp->plan.row0.size() * sizeof(int64_t);
     cudaError_t e = cudaMalloc(&cp->d_row0.ptr, bytes);
@@ -126,7 +127,7 @@ int run_pair(paco_ctx *ctx, const uint8_t *a, int64_t n, const uint8_t *b, int64
     P.wait_limit_ns = ctx->wait_limit_ns;
     P.stall_strip = ctx->test_stall;
     cudaEventRecord(ctx->ev0, st);
-    e = launch_pair_bp(P, pl.C, pl.W, pl.grid, st);
+    e = launch_pair_bp(P, pl.C, pl.W, pl.wpl, pl.grid, st);
     cudaEventRecord(ctx->ev1, st);
     ctx->timed = true;
     ctx->timed_name = "k_pair_bp";

@@ -172,11 +172,13 @@ bool plan_pair(int64_t n, int64_t m, int sms, const PairPlanOptions &o, PairPlan
     out.L = out.transpose ? m : n;
     out.S = out.transpose ? n : m;
     // chunk width: lane k of a strip trails lane 0 by 2k chunks, so the
-    // pipeline's fill grows with C while the per-chunk hand-off cost shrinks;
-    // measured on GB300 the hand-off is already hidden at C = 2, which then
-    // wins whenever the streamed side is long enough to amortise it.
-    out.C = o.chunk ? o.chunk : ((out.S >= 64) ? 2 : 4);
-    const int64_t warps_total = (out.L + kPlanWarpRows - 1) / kPlanWarpRows;
+    // pipeline's fill grows with C while the per-chunk overhead shrinks;
+    // measured on GB300, C = 2 wins on short streamed sides (a 4096-column
+    // table) and C = 4 on long ones (131072 columns, about 3%).
+    out.C = o.chunk ? o.chunk : ((out.S >= 32768) ? 4 : ((out.S >= 64) ? 2 : 4));
+    out.wpl = o.wpl == 2 ? 2 : 1;
+    const int64_t warp_rows = kPlanWarpRows * out.wpl, lane_rows = kPlanLaneRows * out.wpl;
+    const int64_t warps_total = (out.L + warp_rows - 1) / warp_rows;
     // one warp per CTA strip unless the strips would not all be resident at once
     int W = o.warps > 0 ? o.warps : 1;
     W = std::max(1, std::min(W, o.max_warps));
@@ -192,21 +194,21 @@ bool plan_pair(int64_t n, int64_t m, int sms, const PairPlanOptions &o, PairPlan
     }
     out.W = W;
     if (o.schedule == 1) {
-        const int64_t h = (int64_t)W * kPlanWarpRows;
+        const int64_t h = (int64_t)W * warp_rows;
         nstrips = (out.L + h - 1) / h;
         out.row0.resize((size_t)nstrips + 1);
         for (int64_t k = 0; k <= nstrips; ++k) out.row0[(size_t)k] = std::min(out.L, k * h);
     } else {
         // the p-way first division of the PACO partition on rows, p = nstrips,
-        // in lane granules of 31 rows (parts differ by at most one granule)
-        const int64_t G = (out.L + kPlanLaneRows - 1) / kPlanLaneRows;
+        // in lane granules of 31 * wpl rows (parts differ by at most one granule)
+        const int64_t G = (out.L + lane_rows - 1) / lane_rows;
         const std::vector<int64_t> parts = balanced_split(G, nstrips);
         out.row0.resize((size_t)nstrips + 1);
         int64_t acc = 0;
         out.row0[0] = 0;
         for (int64_t k = 0; k < nstrips; ++k) {
             acc += parts[(size_t)k];
-            out.row0[(size_t)k + 1] = std::min(out.L, acc * kPlanLaneRows);
+            out.row0[(size_t)k + 1] = std::min(out.L, acc * lane_rows);
         }
     }
     out.nstrips = (int)nstrips;

@@ -47,17 +47,19 @@ struct PairPlan {
     bool transpose = false;  // true: bits along b (rows of the kernel = b)
     int C = 8;               // columns per lane hand-off
     int W = 4;               // warps per CTA strip
+    int wpl = 1;             // 31-row words per lane (a lane holds 31 * wpl rows)
     int nstrips = 1;         // CTA strips (the p of the balanced split)
     int grid = 1;            // CTAs launched (<= nstrips)
     int64_t L = 0, S = 0;    // kernel rows (bit dimension) and streamed columns
-    std::vector<int64_t> row0;  // nstrips+1 offsets, multiples of 31, row0[nstrips] = L
+    std::vector<int64_t> row0;  // nstrips+1 offsets, multiples of 31 * wpl, row0[nstrips] = L
 };
 
 struct PairPlanOptions {
     int chunk = 0;      // 0: cost model
     int warps = 0;      // 0: default
     int orient = 0;     // 0: bits along the longer string; 1: along a; 2: along b
-    int schedule = 0;   // 0: balanced strips (p-way split); 1: uniform strips of W*992 rows
+    int schedule = 0;   // 0: balanced strips (p-way split); 1: uniform strips of W*992*wpl rows
+    int wpl = 0;        // 31-row words per lane: 0 = planner, 1 or 2
     int max_warps = 7;  // shared-memory limit per CTA
     int resident = 0;   // CTAs that fit on the device at once (0: unknown)
 };

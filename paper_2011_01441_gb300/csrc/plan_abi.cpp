@@ -47,19 +47,23 @@ int paco_plan_partition_deps(int64_t n, int64_t m, int32_t p, int64_t base, int6
 }
 
 int paco_plan_pair(int64_t n, int64_t m, int32_t sms, int32_t chunk, int32_t warps, int32_t orient,
-                   int32_t schedule, paco_pair_plan *out, int64_t *row0, int64_t cap) {
+                   int32_t schedule, int32_t words_per_lane, paco_pair_plan *out, int64_t *row0,
+                   int64_t cap) {
     if (!out) return -1;
     paco::PairPlanOptions o;
     o.chunk = chunk;
     o.warps = warps;
     o.orient = orient;
     o.schedule = schedule;
+    o.wpl = words_per_lane;
     paco::PairPlan pl;
     if (!paco::plan_pair(n, m, sms, o, pl)) return -1;
     out->transpose = pl.transpose ? 1 : 0;
     out->chunk = pl.C;
     out->warps = pl.W;
     out->nstrips = pl.nstrips;
+    out->words_per_lane = pl.wpl;
+    out->pad = 0;
     out->L = pl.L;
     out->S = pl.S;
     if (row0)

@@ -150,22 +150,29 @@ def test_partition_leaf_count_formula(lib):
         assert labels[i] == p * (2 ** (i - 1)) * (p - 1)
 
 
+@pytest.mark.parametrize("wpl", [1, 2])
 @pytest.mark.parametrize("n,m,sms", [(131072, 131072, 148), (131072, 131072, 152),
                                      (1048576, 16384, 152), (16384, 1048576, 152),
                                      (4096, 4096, 152), (1000, 3, 152), (33, 1, 7)])
-def test_pair_plan_balanced_strips(lib, n, m, sms):
-    pl = P.paco_plan_pair(n, m, sms)
+def test_pair_plan_balanced_strips(lib, n, m, sms, wpl):
+    pl = P.paco_plan_pair(n, m, sms, words_per_lane=wpl)
     L = max(n, m)
+    g = 31 * wpl  # rows of one lane: the granule of the balanced split
+    assert pl["words_per_lane"] == wpl
     assert pl["L"] == L and pl["S"] == min(n, m)
     assert pl["transpose"] == (1 if m > n else 0)
     row0 = pl["row0"]
     assert row0[0] == 0 and row0[-1] == L
     h = np.diff(row0)
-    assert np.all(h > 0) and np.all(row0[:-1] % 31 == 0)
-    assert np.all(h <= pl["warps"] * 992)
+    assert np.all(h > 0) and np.all(row0[:-1] % g == 0)
+    assert np.all(h <= pl["warps"] * 32 * g)
     if h.size > 2:
-        assert h[:-1].max() - h[:-1].min() <= 31  # the +-1 granule split of the p-way division
+        assert h[:-1].max() - h[:-1].min() <= g  # the +-1 granule split of the p-way division
     assert pl["chunk"] in (2, 4, 8)
+
+
+def test_pair_plan_default_words_per_lane(lib):
+    assert P.paco_plan_pair(131072, 131072, 152)["words_per_lane"] in (1, 2)
 
 
 def test_pair_plan_options(lib):

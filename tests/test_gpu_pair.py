@@ -74,6 +74,39 @@ def test_chunks_and_strip_heights(ctx, chunk, warps):
     check(ctx, a, b, chunk=chunk, warps=warps)
 
 
+@pytest.mark.parametrize("n,m,chunk,warps", [(7000, 4567, 2, 1), (7000, 4567, 4, 2), (7000, 4567, 8, 3),
+                                              (62, 33, 2, 1), (63, 1, 4, 1), (1985, 2049, 8, 1),
+                                              (3001, 1023, 2, 3), (12345, 2000, 4, 1)])
+def test_two_words_per_lane(ctx, n, m, chunk, warps):
+    """Lanes of two 31-row words (the lower one a chunk behind the upper):
+    ragged lanes, ragged chunks, several strips and warps."""
+    a = W.symbols(n + 3 * m, 0, n, 4)
+    b = W.mutate_rate(a, 4, 0.15, chunk, warps)[:m] if m <= n else W.symbols(n + 3 * m, 1, m, 4)
+    check(ctx, a, b, chunk=chunk, warps=warps, words_per_lane=2)
+
+
+def test_two_words_per_lane_boundaries_and_timeout(ctx):
+    rng = np.random.default_rng(8)
+    for t in range(3):
+        pa = W.symbols(80 + t, 0, int(rng.integers(1, 300)), 20)
+        pb = W.symbols(80 + t, 1, int(rng.integers(1, 300)), 20)
+        a = W.symbols(80 + t, 2, int(rng.integers(2000, 5000)), 20)
+        b = W.symbols(80 + t, 3, int(rng.integers(500, 3000)), 20)
+        H = oracle.lcs_table(np.concatenate([pa, a]), np.concatenate([pb, b]))
+        check(ctx, a, b, H[pa.size, pb.size:].copy(), H[pa.size:, pb.size].copy(),
+              words_per_lane=2, chunk=[2, 4, 8][t])
+    a = W.symbols(91, 0, 9000, 4)
+    b = W.symbols(91, 1, 3000, 4)
+    ctx.set_option(P.OPT_WAIT_LIMIT_NS, 50_000_000)
+    try:
+        with pytest.raises(P.PacoError) as e:
+            run(ctx, a, b, warps=1, test_stall=2, words_per_lane=2)
+        assert e.value.status == P.PACO_ETIMEOUT
+    finally:
+        ctx.set_option(P.OPT_WAIT_LIMIT_NS, 2_000_000_000)
+    check(ctx, a, b, words_per_lane=2)
+
+
 @pytest.mark.parametrize("orient", [1, 2])
 def test_orientations(ctx, orient):
     a = W.symbols(31, 0, 1500, 20)
