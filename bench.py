@@ -305,8 +305,9 @@ def run_gpu(args):
     peaks = _peaks()
     clk = clocks.summary()
     sm_hz = (clk["sm_mhz"] if clk else 2070.0) * 1e6
-    lanes = (plan["L"] + 30) // 31
-    cp_steps = plan["S"] + 2 * plan["chunk"] * lanes
+    wpl = plan.get("words_per_lane", 1)
+    lanes = (plan["L"] + 31 * wpl - 1) // (31 * wpl)
+    cp_steps = plan["S"] + (2 if wpl == 1 else 3) * plan["chunk"] * lanes
     cp_ms = cp_steps * CHAIN_CYCLES_PER_COLUMN / sm_hz * 1e3
     traffic = _profiled_traffic("k_pair_bp_pair131072_launches.md", ["pair_kernels.cu", "bp_device.cuh"]) \
         if args.config == "mutated" else None
@@ -318,6 +319,7 @@ def run_gpu(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": desc, "n": n, "m": m, "engine": "bit-parallel strip pipeline",
                    "chunk": plan["chunk"], "warps_per_cta": plan["warps"], "strips": plan["nstrips"],
+                   "words_per_lane": plan.get("words_per_lane", 1),
                    "l2": "flushed between timed steps (512 MiB write)"},
         "kernel_ms_median": kmed,
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
@@ -332,7 +334,8 @@ def run_gpu(args):
         "critical_path": {"bound": "dependency chain", "model_ms": cp_ms, "measured_ms": kmed,
                           "frac": cp_ms / kmed, "column_steps": cp_steps,
                           "cycles_per_column": CHAIN_CYCLES_PER_COLUMN,
-                          "note": "one lane streams all S columns; lanes trail by 2 chunks each"},
+                          "note": "one lane streams all S columns; lanes trail by 2 (one word per lane) "
+                                  "or 3 (two words) chunks each"},
         "e2e": {"value": e2e_val, "unit": "GCUPS", "h2d_bytes_per_step": n + m,
                 "d2h_bytes_per_step": 4 * (n + 1) + 4 * (m + 1) + 4},
         "gpu_launches": 8 * args.steps,

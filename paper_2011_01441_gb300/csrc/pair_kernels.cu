@@ -45,6 +45,13 @@ template <int WPL> __host__ __device__ constexpr int lane_skew() { return WPL ==
 template <int WPL> __host__ __device__ constexpr int lane_lag() { return lane_skew<WPL>() * 31 + (WPL - 1); }
 // Warp 0's input carry words pass through a shared ring of kSrcSlots words.
 constexpr int kSrcSlots = 64;
+// A match table holds one 32-lane row per symbol and one all-zero row after
+// them: columns outside [0, S) (before the first column while the lanes'
+// pipeline fills, past the last one while it drains) read that row, so an
+// idle lane keeps its state and passes zero carries, and one loop serves
+// fill, steady state and drain.
+constexpr size_t kPairTableBytes = kTableBytes + 128;
+constexpr uint32_t kZeroRow = (uint32_t)kMaxSigma * 128u;
 // Column-word lag of the oldest word a warp still reads behind the word its
 // lane 0 is on (the lower word reuses the upper word's offsets).
 __host__ __device__ constexpr int col_lag_words(int C, int WPL) {
@@ -70,7 +77,7 @@ struct PairSmem {
 __host__ __device__ inline PairSmem pair_smem_layout(int W, int C, int WPL) {
     PairSmem L;
     L.tables = 0;
-    L.colring = (uint32_t)(W * WPL * kTableBytes);
+    L.colring = (uint32_t)(W * WPL * kPairTableBytes);
     L.srcring = L.colring + (uint32_t)(col_slots(C, W, WPL) + 2) * 128u;
     L.rings = L.srcring + (uint32_t)kSrcSlots * 4u;
     L.ctrl = L.rings + (uint32_t)(W * kRing * 8);
@@ -129,16 +136,16 @@ __global__ void __launch_bounds__(256, 1) k_pair_bp(const PairArgs P) {
     const uint64_t *ring_in = rings + (size_t)(w > 0 ? w - 1 : 0) * kRing;  // written by warp w-1
     volatile int *cons = reinterpret_cast<volatile int *>(smem + lay.ctrl + 8);
     // table of word x of this warp (x = 0 upper, 1 lower)
-    uint32_t *pm0 = reinterpret_cast<uint32_t *>(smem + (size_t)(w < W ? w * WPL : 0) * kTableBytes);
-    uint32_t *pm1 = pm0 + (WPL == 2 ? kTableBytes / 4 : 0);
+    uint32_t *pm0 = reinterpret_cast<uint32_t *>(smem + (size_t)(w < W ? w * WPL : 0) * kPairTableBytes);
+    uint32_t *pm1 = pm0 + (WPL == 2 ? kPairTableBytes / 4 : 0);
     const uint32_t pm_lane0 = (uint32_t)__cvta_generic_to_shared(pm0 + lane);
     const uint32_t pm_lane1 = (uint32_t)__cvta_generic_to_shared(pm1 + lane);
 
     if (w < W)
-        for (int c = 0; c < kMaxSigma * WPL; ++c) pm0[c * 32 + lane] = 0u;
-    // every ring slot holds a valid table offset from the start
+        for (int c = 0; c < (kMaxSigma + 1) * WPL; ++c) pm0[c * 32 + lane] = 0u;
+    // every ring slot holds a valid table offset (the zero row) from the start
     for (int i = threadIdx.x; i < (R + 2) * 32; i += blockDim.x)
-        reinterpret_cast<uint32_t *>(smem + lay.colring)[i] = 0u;
+        reinterpret_cast<uint32_t *>(smem + lay.colring)[i] = kZeroRow;
 
     constexpr int K = 32 / C;                       // steps per 32-column word
     constexpr int kSk = lane_skew<WPL>();
@@ -146,13 +153,11 @@ __global__ void __launch_bounds__(256, 1) k_pair_bp(const PairArgs P) {
     constexpr int kFlushStep = (kLag - 1) % K;      // step at which lane 31 completes a word
     constexpr int kLagW = col_lag_words(C, WPL);
     constexpr int kRowsLane = kLaneRows * WPL;
-    const int64_t nch = P.nchunks;
-    const int last_valid = (int)(P.S - (nch - 1) * C);
-    const int64_t nch_full = (last_valid == C) ? nch : nch - 1;
     const int64_t nwords = P.nwords;
-    const int64_t nouter = (nch + kLag + K - 1) / K;
-    const int64_t u_fast0 = (kLag + K - 1) / K;
-    const int64_t u_fast1 = nch_full / K;           // exclusive
+    // words lane 0 runs over: the real ones, then zero-row words until the
+    // last lane has finished the last real word
+    const int64_t nouter = (nwords * K + kLag + K - 1) / K;
+    const int64_t nvwords = nouter + 2;             // words the producer writes (with the prefetch)
 
     for (;;) {
         __syncthreads();
@@ -183,18 +188,23 @@ __global__ void __launch_bounds__(256, 1) k_pair_bp(const PairArgs P) {
             int64_t qc = 0, qs = 0;
             int idle = 0;
             uint64_t t_idle = global_ns();
-            while (qc < nwords || qs < nwords) {
+            {   // the words before column 0 (read while the lanes' pipeline fills): zero rows
+                uint32_t *ring = reinterpret_cast<uint32_t *>(smem + lay.colring);
+                for (int j = 1; j <= kLagW + 1; ++j) ring[(uint32_t)((R - j) & (R - 1)) * 32 + lane] = kZeroRow;
+                __syncwarp();
+            }
+            while (qc < nvwords || qs < nwords) {
                 bool progress = false;
                 int minc = cons[0];
                 for (int v = 1; v < W; ++v) minc = min(minc, cons[v]);
-                const int64_t lim_c = min(nwords, (int64_t)minc - 1 - kLagW + R);
+                const int64_t lim_c = min(nvwords, (int64_t)minc - 1 - kLagW + R);
                 if (qc < lim_c) {
                     const int64_t qe = min(lim_c, qc + 4);
                     uint32_t o[4];
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
                         const int64_t col = (qc + k) * 32 + lane;
-                        o[k] = (qc + k < qe && col < P.S) ? (uint32_t)__ldg(P.b + col) * 128u : 0u;
+                        o[k] = (qc + k < qe && col < P.S) ? (uint32_t)__ldg(P.b + col) * 128u : kZeroRow;
                     }
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
@@ -314,10 +324,11 @@ __global__ void __launch_bounds__(256, 1) k_pair_bp(const PairArgs P) {
         uint32_t oprev[C];      // two words: this step's offsets, for the lower word next step
         uint32_t Mlow[C];       // two words: the lower word's match words for this step
         bool ok = true;
+        int cons_seen = 0;  // warps w > 0 downstream: last consumption count read
         const uint32_t ring_tag0 = 1;
         for (int64_t u = 0; u < nouter; ++u) {
             // inputs of this word: column offsets up to word u+1, the input carry word u
-            const int need_c = (int)min(u + 2, nwords);
+            const int need_c = (int)min(u + 2, nvwords);
             const int need_s = (w == 0 && u < nwords) ? (int)(u + 1) : 0;
             const uint64_t *rw = (w > 0 && u < nwords) ? ring_in + (u % kRing) : nullptr;
             uint32_t srcw = 0;
@@ -345,10 +356,6 @@ __global__ void __launch_bounds__(256, 1) k_pair_bp(const PairArgs P) {
             // this lane's column of step 0 (upper word) and its place in the ring
             const int64_t c0 = u * 32 - (int64_t)kSk * C * lane;
             const uint32_t cbase = col_ring + (uint32_t)(((c0 >> 5) & (R - 1)) * 128) + (uint32_t)((c0 & 31) * 4);
-            // the lower word's column of step 0 (one chunk behind) in the ring
-            const int64_t c0l = c0 - C;
-            const uint32_t cbase_l =
-                col_ring + (uint32_t)(((c0l >> 5) & (R - 1)) * 128) + (uint32_t)((c0l & 31) * 4);
             auto offs_at = [&](uint32_t addr, uint32_t (&o)[C]) {
                 if constexpr (C == 2) {
                     uint32_t x, y;
@@ -369,129 +376,72 @@ __global__ void __launch_bounds__(256, 1) k_pair_bp(const PairArgs P) {
                 }
             };
             if (lane == 0) sr[0] = srcw;
-            if (u >= u_fast0 && u < u_fast1) {
-                // ---------- steady state: every word of every lane on a full chunk ----------
-                // Software pipeline: offsets two steps ahead, match words one
-                // step ahead, the carry hand-off after the step's columns (its
-                // result is used two steps later), so a warp issuing in order
-                // never waits on a shared load or a shuffle before a column.
-                if (u == u_fast0) {  // later words: carried over from the step before
-                    uint32_t o0[C];
-                    offs_at(cbase, o0);
-                    match_words<C>(pm_lane0, o0, Mcur);
-                    if constexpr (WPL == 2) {
-                        uint32_t om[C];
-                        offs_at(cbase_l, om);  // the lower word's chunk: one behind
-                        match_words<C>(pm_lane1, om, Mlow);
-#pragma unroll
-                        for (int jj = 0; jj < C; ++jj) oprev[jj] = o0[jj];
-                    }
-                    offs_at(cbase + (uint32_t)(C * 4), onext);
-                }
-#pragma unroll
-                for (int i = 0; i < K; ++i) {
-                    uint32_t onext2[C], Mnext[C], Mlow_next[C];
-                    offs_at(cbase + (uint32_t)((i + 2) * C * 4), onext2);
-                    match_words<C>(pm_lane0, onext, Mnext);
-                    if constexpr (WPL == 2) match_words<C>(pm_lane1, oprev, Mlow_next);
-                    if (lane != 0) sr[0] = cin_cur << (32 - C);
-                    if constexpr (WPL == 2) {
-                        sr[1] = cw[0] << (32 - C);  // the upper word's carries of the step before
-#pragma unroll
-                        for (int jj = 0; jj < C; ++jj) {
-                            column31c(Sv[0], Yv[0], sr[0], cw[0], Mcur[jj]);
-                            column31c(Sv[1], Yv[1], sr[1], cw[1], Mlow[jj]);
-                        }
-                    } else {
-#pragma unroll
-                        for (int jj = 0; jj < C; ++jj) column31c(Sv[0], Yv[0], sr[0], cw[0], Mcur[jj]);
-                    }
-                    const uint32_t recv = __shfl_up_sync(kFull, cw[WPL - 1], 1);
-                    cin_cur = cin_nxt;
-                    cin_nxt = recv;
+            // Software pipeline: offsets two steps ahead, match words one step
+            // ahead, the carry hand-off after the step's columns (its result is
+            // used two steps later), so a warp issuing in order never waits on
+            // a shared load or a shuffle before a column.  Columns outside
+            // [0, S) read the zero row: no per-lane activity tests.
+            if (u == 0) {  // later words: carried over from the step before
+                uint32_t o0[C];
+                offs_at(cbase, o0);
+                match_words<C>(pm_lane0, o0, Mcur);
+                if constexpr (WPL == 2) {
+                    // the lower word's chunk of step 0 (one behind) lies before column 0
 #pragma unroll
                     for (int jj = 0; jj < C; ++jj) {
-                        Mcur[jj] = Mnext[jj];
-                        if constexpr (WPL == 2) {
-                            Mlow[jj] = Mlow_next[jj];
-                            oprev[jj] = onext[jj];
-                        }
-                        onext[jj] = onext2[jj];
-                    }
-                    if (i == kFlushStep) {  // lane 31 completes word wq (a predicated store)
-                        const int64_t wq = ((ubase + i - kLag) * C) >> 5;
-                        if (w + 1 < W) {
-                            // on a timeout the error is raised and every later wait
-                            // returns at once, so the strip ends with its result void
-                            if (lane == 31)
-                                wait_consumed(cons + w + 1, (int)(wq - kRing + 1), P.err, P.wait_limit_ns);
-                            st_volatile_shared_u64_if(lane == 31, ring_out_s + (uint32_t)((wq % kRing) * 8),
-                                                      ((uint64_t)(uint32_t)(wq + ring_tag0) << 32) | cw[WPL - 1]);
-                        } else {
-                            st_relaxed_u64_if(lane == 31, dst_row + wq, ((uint64_t)P.epoch << 32) | cw[WPL - 1]);
-                        }
+                        Mlow[jj] = 0u;
+                        oprev[jj] = o0[jj];
                     }
                 }
-            } else {
-                // ---------- fill / drain: the same windows, per-lane activity ----------
+                offs_at(cbase + (uint32_t)(C * 4), onext);
+            }
 #pragma unroll
-                for (int i = 0; i < K; ++i) {
-                    const int64_t q = ubase + i - (int64_t)kSk * lane;  // the upper word's chunk
-                    uint32_t oq[C];
-                    offs_at(cbase + (uint32_t)(i * C * 4), oq);
-                    bool last_act = false;
-                    int64_t qlast = q;
+            for (int i = 0; i < K; ++i) {
+                uint32_t onext2[C], Mnext[C], Mlow_next[C];
+                offs_at(cbase + (uint32_t)((i + 2) * C * 4), onext2);
+                match_words<C>(pm_lane0, onext, Mnext);
+                if constexpr (WPL == 2) match_words<C>(pm_lane1, oprev, Mlow_next);
+                if (lane != 0) sr[0] = cin_cur << (32 - C);
+                if constexpr (WPL == 2) {
+                    sr[1] = cw[0] << (32 - C);  // the upper word's carries of the step before
+#pragma unroll
+                    for (int jj = 0; jj < C; ++jj) {
+                        column31c(Sv[0], Yv[0], sr[0], cw[0], Mcur[jj]);
+                        column31c(Sv[1], Yv[1], sr[1], cw[1], Mlow[jj]);
+                    }
+                } else {
+#pragma unroll
+                    for (int jj = 0; jj < C; ++jj) column31c(Sv[0], Yv[0], sr[0], cw[0], Mcur[jj]);
+                }
+                const uint32_t recv = __shfl_up_sync(kFull, cw[WPL - 1], 1);
+                cin_cur = cin_nxt;
+                cin_nxt = recv;
+#pragma unroll
+                for (int jj = 0; jj < C; ++jj) {
+                    Mcur[jj] = Mnext[jj];
                     if constexpr (WPL == 2) {
-                        // lower word first: its carries are the upper word's of the step before
-                        const int64_t ql = q - 1;
-                        const bool actl = (ql >= 0) && (ql < nch);
-                        uint32_t ol[C];
-                        offs_at(cbase_l + (uint32_t)(i * C * 4), ol);
-                        if (actl) {
-                            sr[1] = cw[0] << (32 - C);
-                            if (ql == nch - 1 && last_valid < C) {
-#pragma unroll
-                                for (int jj = 0; jj < C; ++jj)
-                                    if (jj < last_valid) column31c(Sv[1], Yv[1], sr[1], cw[1], lds_u32(pm_lane1 + ol[jj]));
-                                cw[1] <<= (C - last_valid);
-                            } else {
-#pragma unroll
-                                for (int jj = 0; jj < C; ++jj)
-                                    column31c(Sv[1], Yv[1], sr[1], cw[1], lds_u32(pm_lane1 + ol[jj]));
-                            }
-                        }
-                        last_act = actl;
-                        qlast = ql;
+                        Mlow[jj] = Mlow_next[jj];
+                        oprev[jj] = onext[jj];
                     }
-                    const bool act = (q >= 0) && (q < nch);
-                    if (act) {
-                        if (lane != 0) sr[0] = cin_cur << (32 - C);
-                        if (q == nch - 1 && last_valid < C) {
-#pragma unroll
-                            for (int jj = 0; jj < C; ++jj)
-                                if (jj < last_valid) column31c(Sv[0], Yv[0], sr[0], cw[0], lds_u32(pm_lane0 + oq[jj]));
-                            cw[0] <<= (C - last_valid);  // keep the chunk MSB-first
-                        } else {
-#pragma unroll
-                            for (int jj = 0; jj < C; ++jj)
-                                column31c(Sv[0], Yv[0], sr[0], cw[0], lds_u32(pm_lane0 + oq[jj]));
+                    onext[jj] = onext2[jj];
+                }
+                if (i == kFlushStep) {  // lane 31 completes word wq (a predicated store)
+                    const int64_t wq = ((ubase + i - kLag) * C) >> 5;
+                    const bool fl = lane == 31 && wq >= 0 && wq < nwords;
+                    if (w + 1 < W) {
+                        // the next warp has consumed up to cons_seen: wait only when
+                        // the ring slot may still be unread.  On a timeout the
+                        // error is raised and every later wait returns at once,
+                        // so the strip ends with its result void.
+                        const int need = (int)(wq - kRing + 1);
+                        if (__any_sync(kFull, fl) && need > cons_seen) {
+                            if (fl) wait_consumed(cons + w + 1, need, P.err, P.wait_limit_ns);
+                            cons_seen = cons[w + 1];
                         }
-                    }
-                    if constexpr (WPL == 1) last_act = act;
-                    const uint32_t recv = __shfl_up_sync(kFull, cw[WPL - 1], 1);
-                    cin_cur = cin_nxt;
-                    cin_nxt = recv;
-                    const bool fl = lane == 31 && last_act && (((qlast + 1) % K) == 0 || qlast == nch - 1);
-                    if (__any_sync(kFull, fl)) {
-                        const int64_t wq = (qlast * C) >> 5;
-                        const uint32_t gw = cw[WPL - 1] << ((32 - C - ((qlast * C) & 31)) & 31);
-                        if (w + 1 < W) {
-                            if (fl) wait_consumed(cons + w + 1, (int)(wq - kRing + 1), P.err, P.wait_limit_ns);
-                            st_volatile_shared_u64_if(fl, ring_out_s + (uint32_t)(((wq % kRing) & (kRing - 1)) * 8),
-                                                      ((uint64_t)(uint32_t)(wq + ring_tag0) << 32) | gw);
-                        } else {
-                            st_relaxed_u64_if(fl, dst_row + (fl ? wq : 0), ((uint64_t)P.epoch << 32) | gw);
-                        }
+                        st_volatile_shared_u64_if(fl, ring_out_s + (uint32_t)(((wq % kRing) & (kRing - 1)) * 8),
+                                                  ((uint64_t)(uint32_t)(wq + ring_tag0) << 32) | cw[WPL - 1]);
+                    } else {
+                        st_relaxed_u64_if(fl, dst_row + (fl ? wq : 0), ((uint64_t)P.epoch << 32) | cw[WPL - 1]);
                     }
                 }
             }

@@ -171,12 +171,24 @@ bool plan_pair(int64_t n, int64_t m, int sms, const PairPlanOptions &o, PairPlan
     out.transpose = o.orient == 2 || (o.orient == 0 && m > n);
     out.L = out.transpose ? m : n;
     out.S = out.transpose ? n : m;
-    // chunk width: lane k of a strip trails lane 0 by 2k chunks, so the
+    // chunk width: lane k of a strip trails lane 0 by a few chunks, so the
     // pipeline's fill grows with C while the per-chunk overhead shrinks;
-    // measured on GB300, C = 2 wins on short streamed sides (a 4096-column
-    // table) and C = 4 on long ones (131072 columns, about 3%).
-    out.C = o.chunk ? o.chunk : ((out.S >= 32768) ? 4 : ((out.S >= 64) ? 2 : 4));
-    out.wpl = o.wpl == 2 ? 2 : 1;
+    // measured on GB300, C = 2 wins from a 4096-column streamed side up.
+    out.C = o.chunk ? o.chunk : ((out.S >= 64) ? 2 : 4);
+    // words per lane: each lane streams all S columns after a fill of
+    // (lanes x skew x C) column steps; two words per lane halve the lanes and
+    // take a longer skew and step (measured: 1.18x the step time, skew 3
+    // chunks against 2).  Pick the smaller modelled time.
+    if (o.wpl == 1 || o.wpl == 2) {
+        out.wpl = o.wpl;
+    } else {
+        auto cost = [&](int wpl) {
+            const double lanes = (double)((out.L + kPlanLaneRows * wpl - 1) / (kPlanLaneRows * wpl));
+            const double skew = wpl == 1 ? 2.0 : 3.0, step = wpl == 1 ? 1.0 : 1.18;
+            return step * ((double)out.S + lanes * skew * out.C);
+        };
+        out.wpl = cost(2) < cost(1) ? 2 : 1;
+    }
     const int64_t warp_rows = kPlanWarpRows * out.wpl, lane_rows = kPlanLaneRows * out.wpl;
     const int64_t warps_total = (out.L + warp_rows - 1) / warp_rows;
     // one warp per CTA strip unless the strips would not all be resident at once
