@@ -60,8 +60,8 @@ struct ColJob {
     int32_t pad;
 };
 
-// Symbols outside the declared alphabet (>= sigma) point at the table's
-// spare all-zero row and raise PACO_EINVAL.
+// Symbol c uses match-table row c + 1; row 0 is all zero.  Symbols outside
+// the declared alphabet (>= sigma) point at row 0 and raise PACO_EINVAL.
 __global__ void k_pair_column_offsets(const uint8_t *a_cat, const uint8_t *b_cat, const ColJob *cj,
                                       uint32_t *coffs, int sigma, int *err) {
     const ColJob J = cj[blockIdx.x];
@@ -71,7 +71,9 @@ __global__ void k_pair_column_offsets(const uint8_t *a_cat, const uint8_t *b_cat
         uint32_t c = src[j];
         if ((int)c >= sigma) {
             bad = true;
-            c = (uint32_t)sigma;
+            c = 0u;
+        } else {
+            c += 1u;
         }
         coffs[J.dst + j] = c * 128u;
     }
@@ -92,7 +94,7 @@ struct BatchArgs {
     const uint32_t *epoch_dev;
     long long wait_limit_ns;
     int sigma;       // declared alphabet: symbols are < sigma
-    int table_rows;  // rows of the per-warp match table (sigma, plus a zero row when < 256)
+    int table_rows;  // rows of the per-warp match table: the zero row, then one per symbol
     int cls_chunk[4];  // chunk width of each size class
 };
 
@@ -110,7 +112,7 @@ constexpr int kColAhead = 8;
 // real lane: that lane hands the bottom row on.
 template <int C>
 static __device__ __forceinline__ void batch_job(const BatchArgs &P, const SegJob &J, const int lane, uint32_t *pm,
-                                                 const uint32_t pm_lane, const uint32_t col_ring,
+                                                 const uint32_t pm_lane, uint32_t *cols_ptr, const uint32_t col_ring,
                                                  const uint32_t src_ring, const uint32_t epoch) {
     constexpr int K = 32 / C;
     {
@@ -133,7 +135,7 @@ static __device__ __forceinline__ void batch_job(const BatchArgs &P, const SegJo
         for (int r = 0; r < kLaneRows; ++r) {
             if (r < nreal) {
                 const uint32_t ch = (aw[r >> 2] >> ((r & 3) * 8)) & 0xffu;
-                if ((int)ch < P.sigma) pm[ch * 32 + lane] |= 1u << r;
+                if ((int)ch < P.sigma) pm[(ch + 1) * 32 + lane] |= 1u << r;
                 else badsym = true;
             }
         }
@@ -141,16 +143,13 @@ static __device__ __forceinline__ void batch_job(const BatchArgs &P, const SegJo
         uint32_t V = 0xffffffffu;  // zero first column: no vertical steps; bit 31 held at 1
         __syncwarp();
 
-        const int64_t nch = (S + C - 1) / C;
-        const int last_valid = (int)(S - (nch - 1) * C);
-        const int64_t nch_full = (last_valid == C) ? nch : nch - 1;
         const int64_t nwords = (S + 31) >> 5;
         const int64_t npairs = (nwords + 1) >> 1;
         const int last = (J.nrows - 1) / kLaneRows;      // last real lane: the pipeline's end
         const int flush_i = (last + K - 1) % K;         // step at which it completes a word
-        const int64_t nouter = (nch + last + K - 1) / K;
-        const int64_t u_fast0 = (last + K - 1) / K;  // first word with every real lane on a full chunk
-        const int64_t u_fast1 = nch_full / K;      // exclusive
+        // words lane 0 runs over: the real ones, then zero-row words until the
+        // last lane has finished the last real word
+        const int64_t nouter = (nwords * K + last + K - 1) / K;
         const bool in_global = (J.flags & kInGlobal) != 0;
         const bool out_global = (J.flags & kOutGlobal) != 0;
         const uint64_t *src_row = P.hbuf + J.hin;
@@ -170,15 +169,15 @@ static __device__ __forceinline__ void batch_job(const BatchArgs &P, const SegJo
 
         uint32_t cw = 0;      // this lane's carry-outs, newest in bit 0 (never reset)
         uint32_t sr = 0;      // carry-ins, next one in bit 31
-        uint32_t total = 0;   // lane 31 of a final segment: set bits of the bottom row
+        uint32_t total = 0;   // the last lane of a final segment: set bits of the bottom row
         bool ok = true;
         // lanes 0..7 copy one 32-column word (16 bytes each); lanes 8..15 the
-        // mirror copy when the word lands in slot 0 or 1
+        // mirror copy when the word lands in slot 0 or 1.  Columns at or past
+        // S are zero-filled: offset 0 is the all-zero match row.
         auto issue_cols = [&](int64_t wd) {
             const int slot = (int)(wd % kColRing);
             const int part = lane & 7;
-            const bool mine = wd < nwords && (lane < 8 || (lane < 16 && slot < 2));
-            if (mine) {
+            if (lane < 8 || (lane < 16 && slot < 2)) {
                 const int64_t col = wd * 32 + part * 4;
                 const int64_t rem = S - col;
                 const int bytes = rem >= 4 ? 16 : (rem > 0 ? (int)rem * 4 : 0);
@@ -209,6 +208,13 @@ static __device__ __forceinline__ void batch_job(const BatchArgs &P, const SegJo
                 }
             }
         };
+        // the words before column 0 (read while the lanes' pipeline fills): zero rows
+        {
+            constexpr int kBefore = (31 * C + 31) / 32 + 1;
+            uint32_t *ring = cols_ptr;
+            for (int j = 1; j <= kBefore; ++j) ring[(kColRing - j) * 32 + lane] = 0u;
+            __syncwarp();
+        }
         for (int d = 0; d < kColAhead; ++d) issue_cols(d);
         for (int64_t u = 0; u < nouter; ++u) {
             asm volatile("cp.async.wait_group %0;" ::"n"(kColAhead - 1) : "memory");
@@ -236,60 +242,28 @@ static __device__ __forceinline__ void batch_job(const BatchArgs &P, const SegJo
             // this lane's column of step 0 (lane k trails lane 0 by k chunks) in the ring
             const int64_t c0 = u * 32 - (int64_t)C * lane;
             const uint32_t cbase = col_ring + (uint32_t)(((c0 >> 5) & (kColRing - 1)) * 128) + (uint32_t)((c0 & 31) * 4);
-            if (u >= u_fast0 && u < u_fast1) {
-                // ---------- steady state: every lane on a full chunk ----------
-                uint32_t ocur[C], onext[C];
-                offs_at(cbase, ocur);
+            // one loop for fill, steady state and drain: columns outside [0, S)
+            // read the zero row, so an idle lane keeps its state and passes
+            // zero carries
+            uint32_t ocur[C], onext[C];
+            offs_at(cbase, ocur);
 #pragma unroll
-                for (int i = 0; i < K; ++i) {
-                    if (i + 1 < K) offs_at(cbase + (uint32_t)((i + 1) * C * 4), onext);
-                    const uint32_t up = __shfl_up_sync(kFull, cw, 1);
-                    if (lane != 0) sr = up << (32 - C);
+            for (int i = 0; i < K; ++i) {
+                if (i + 1 < K) offs_at(cbase + (uint32_t)((i + 1) * C * 4), onext);
+                const uint32_t up = __shfl_up_sync(kFull, cw, 1);
+                if (lane != 0) sr = up << (32 - C);
 #pragma unroll
-                    for (int jj = 0; jj < C; ++jj) column31v(V, sr, cw, lds_u32(pm_lane + ocur[jj]));
+                for (int jj = 0; jj < C; ++jj) column31v(V, sr, cw, lds_u32(pm_lane + ocur[jj]));
 #pragma unroll
-                    for (int jj = 0; jj < C; ++jj) ocur[jj] = onext[jj];
-                    if (i == flush_i) {  // the last lane completes word wq
-                        const int64_t wq = ((ubase + i - last) * C) >> 5;
-                        if (out_global) {
-                            st_relaxed_u64_if(lane == last, dst_row + wq, ((uint64_t)epoch << 32) | cw);
-                        } else if (lane == last) {
-                            total += __popc(cw);
-                            if (keep_bits) bout[wq] = cw;
-                        }
-                    }
-                }
-            } else {
-                // ---------- fill / drain: per-lane activity ----------
-#pragma unroll
-                for (int i = 0; i < K; ++i) {
-                    const int64_t q = ubase + i - lane;
-                    const uint32_t up = __shfl_up_sync(kFull, cw, 1);
-                    const bool act = (q >= 0) && (q < nch);
-                    uint32_t oq[C];
-                    offs_at(cbase + (uint32_t)(i * C * 4), oq);
-                    if (act) {
-                        if (lane != 0) sr = up << (32 - C);
-                        if (q == nch - 1 && last_valid < C) {
-#pragma unroll
-                            for (int jj = 0; jj < C; ++jj)
-                                if (jj < last_valid) column31v(V, sr, cw, lds_u32(pm_lane + oq[jj]));
-                            cw <<= (C - last_valid);  // keep the chunk MSB-first
-                        } else {
-#pragma unroll
-                            for (int jj = 0; jj < C; ++jj) column31v(V, sr, cw, lds_u32(pm_lane + oq[jj]));
-                        }
-                    }
-                    const bool fl = lane == last && act && ((((q + 1) * C) & 31) == 0 || q == nch - 1);
-                    if (__any_sync(kFull, fl)) {
-                        const int64_t wq = (q * C) >> 5;
-                        const uint32_t gw = cw << ((32 - C - ((q * C) & 31)) & 31);
-                        if (out_global) {
-                            st_relaxed_u64_if(fl, dst_row + (fl ? wq : 0), ((uint64_t)epoch << 32) | gw);
-                        } else if (fl) {
-                            total += __popc(gw);
-                            if (keep_bits) bout[wq] = gw;
-                        }
+                for (int jj = 0; jj < C; ++jj) ocur[jj] = onext[jj];
+                if (i == flush_i) {  // the last lane completes word wq
+                    const int64_t wq = ((ubase + i - last) * C) >> 5;
+                    const bool fl = lane == last && wq >= 0 && wq < nwords;
+                    if (out_global) {
+                        st_relaxed_u64_if(fl, dst_row + (fl ? wq : 0), ((uint64_t)epoch << 32) | cw);
+                    } else if (fl) {
+                        total += __popc(cw);
+                        if (keep_bits) bout[wq] = cw;
                     }
                 }
             }
@@ -303,7 +277,7 @@ static __device__ __forceinline__ void batch_job(const BatchArgs &P, const SegJo
         for (int r = 0; r < kLaneRows; ++r) {
             if (r < nreal) {
                 const uint32_t ch = (aw[r >> 2] >> ((r & 3) * 8)) & 0xffu;
-                if ((int)ch < P.sigma) pm[ch * 32 + lane] = 0u;
+                if ((int)ch < P.sigma) pm[(ch + 1) * 32 + lane] = 0u;
             }
         }
         __syncwarp();
@@ -334,9 +308,9 @@ __global__ void __launch_bounds__(32) k_batch(const BatchArgs P) {
         // the chunk width of the job's size class
         const int cl = (int)((J.flags >> kClassShift) & 3u);  // (no dynamic index into the parameters)
         const int C = cl == 0 ? P.cls_chunk[0] : (cl == 1 ? P.cls_chunk[1] : (cl == 2 ? P.cls_chunk[2] : P.cls_chunk[3]));
-        if (C == 2) batch_job<2>(P, J, lane, pm, pm_lane, col_ring, src_ring, epoch);
-        else if (C == 4) batch_job<4>(P, J, lane, pm, pm_lane, col_ring, src_ring, epoch);
-        else batch_job<8>(P, J, lane, pm, pm_lane, col_ring, src_ring, epoch);
+        if (C == 2) batch_job<2>(P, J, lane, pm, pm_lane, s_cols, col_ring, src_ring, epoch);
+        else if (C == 4) batch_job<4>(P, J, lane, pm, pm_lane, s_cols, col_ring, src_ring, epoch);
+        else batch_job<8>(P, J, lane, pm, pm_lane, s_cols, col_ring, src_ring, epoch);
     }
 }
 
@@ -428,7 +402,7 @@ __global__ void k_batch_prefix(const PrefixJob *pj, const uint32_t *bbits, const
 cudaError_t launch_batch(const BatchArgs &a, int grid, cudaStream_t st) {
     const size_t smem = (size_t)a.table_rows * 32 * 4;
     cudaError_t e = cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(kMaxSigma * 32 * 4));
+                                         (int)((kMaxSigma + 1) * 32 * 4));
     if (e != cudaSuccess) return e;
     k_batch<<<grid, 32, smem, st>>>(a);
     return cudaGetLastError();
@@ -436,7 +410,7 @@ cudaError_t launch_batch(const BatchArgs &a, int grid, cudaStream_t st) {
 
 int occupancy_for(int table_rows) {
     const size_t smem = (size_t)table_rows * 32 * 4;
-    if (cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kMaxSigma * 32 * 4)) !=
+    if (cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)((kMaxSigma + 1) * 32 * 4)) !=
         cudaSuccess)
         return 1;
     int nb = 0;
@@ -444,7 +418,7 @@ int occupancy_for(int table_rows) {
     return std::max(1, nb);
 }
 
-int table_rows_for(int sigma) { return sigma >= kMaxSigma ? kMaxSigma : sigma + 1; }
+int table_rows_for(int sigma) { return (sigma >= kMaxSigma ? kMaxSigma : sigma) + 1; }
 
 struct Layout {
     std::vector<SegJob> jobs;
