@@ -421,7 +421,7 @@ def run_batch_bench(args):
 
 
 def run_serve_bench(args):
-    """Poisson stream of requests through paco_lcs_submit / paco_lcs_poll at
+    """Poisson stream of requests through paco_lcs_submit_many / paco_lcs_poll_many at
     fractions of the saturating rate; p50/p99 latency beside throughput, and
     the same arrival schedule served one pair per launch (FIFO) as the plain
     comparison."""
@@ -449,27 +449,34 @@ def run_serve_bench(args):
     for frac in (0.5, 0.9, 1.0):
         lam = frac * lam_sat
         arr = W.poisson_arrivals(7, nreq, lam)
-        tickets = [None] * nreq
-        done_t = [None] * nreq
+        tickets = np.zeros(nreq, dtype=np.uint64)
+        done_t = np.full(nreq, np.nan)
+        submitted = [0]
         t_start = time.perf_counter()
 
         def submitter():
-            for k in range(nreq):
-                delay = arr[k] - (time.perf_counter() - t_start)
-                if delay > 0:
-                    time.sleep(delay)
-                tickets[k] = P.paco_lcs_submit(ctx, reqs[k].a, reqs[k].b)
+            # every request whose arrival time has passed goes in one call
+            k = 0
+            while k < nreq:
+                now = time.perf_counter() - t_start
+                j = int(np.searchsorted(arr, now, side="right"))
+                if j <= k:
+                    time.sleep(max(0.0, min(arr[k] - now, 0.0005)))
+                    continue
+                tickets[k:j] = P.paco_lcs_submit_many(ctx, a_cat, a_off[k:j + 1], b_cat, b_off[k:j + 1])
+                k = j
+                submitted[0] = k
         thr = th.Thread(target=submitter)
         thr.start()
-        pending = set(range(nreq))
-        while pending:
-            for k in list(pending):
-                if tickets[k] is None:
-                    continue
-                r = P.paco_lcs_poll(ctx, tickets[k])
-                if r is not None:
-                    done_t[k] = time.perf_counter() - t_start
-                    pending.discard(k)
+        pending = np.arange(nreq)
+        while pending.size:
+            ready = pending[pending < submitted[0]]
+            if ready.size:
+                st, _ = P.paco_lcs_poll_many(ctx, tickets[ready])
+                fin = ready[st != P.PACO_PENDING]
+                if fin.size:
+                    done_t[fin] = time.perf_counter() - t_start
+                    pending = np.setdiff1d(pending, fin, assume_unique=True)
             time.sleep(0.0002)
         thr.join()
         lat = np.array(done_t) - arr

@@ -217,6 +217,24 @@ int paco_lcs_submit(paco_ctx *ctx, const uint8_t *a, int64_t n,
 int paco_lcs_poll(paco_ctx *ctx, uint64_t ticket, int32_t *len,
                   int32_t *row_out, int32_t *col_out);
 
+/* Submit `count` requests at once (one lock and one wake-up of the engine):
+ * request k is a_cat[a_off[k] .. a_off[k+1]) against b_cat[b_off[k] ..
+ * b_off[k+1]), all HOST buffers copied before the call returns; lengths only
+ * (no boundaries).  tickets[count] receives the tickets.  Returns PACO_OK,
+ * PACO_EINVAL for a bad argument (nothing submitted), or PACO_EBUSY when a
+ * request does not fit the budget or the queue is full: then *n_submitted
+ * (if not NULL) tells how many of the first requests were taken. */
+int paco_lcs_submit_many(paco_ctx *ctx, const uint8_t *a_cat, const int64_t *a_off,
+                         const uint8_t *b_cat, const int64_t *b_off, int64_t count,
+                         uint64_t *tickets, int64_t *n_submitted);
+
+/* Poll `count` length-only tickets at once: for each finished one, len[k]
+ * and status[k] (PACO_OK or its device error) are written and the ticket is
+ * released; unfinished ones get status[k] = PACO_PENDING, unknown ones
+ * PACO_ENOTFOUND.  *n_done (if not NULL) receives the number finished. */
+int paco_lcs_poll_many(paco_ctx *ctx, const uint64_t *tickets, int64_t count, int32_t *len,
+                       int32_t *status, int64_t *n_done);
+
 /* Serving statistics since the context was created (host monotonic clock,
  * seconds): completed requests, cells, queue and in-flight counts. */
 typedef struct paco_serve_stats {

@@ -89,6 +89,8 @@ def load():
         "paco_lcs_boundaries_static": ([P, I64, P, I64, P, P, P, P], INT),
         "paco_lcs_submit": ([P, P, I64, P, I64, INT, ctypes.POINTER(ctypes.c_uint64)], INT),
         "paco_lcs_poll": ([P, ctypes.c_uint64, P, P, P], INT),
+        "paco_lcs_submit_many": ([P, P, P, P, P, I64, P, P], INT),
+        "paco_lcs_poll_many": ([P, P, I64, P, P, P], INT),
         "paco_serve_get_stats": ([P, ctypes.POINTER(PacoServeStats)], INT),
         "paco_measure_int_peak": ([P, INT, ctypes.POINTER(ctypes.c_double), P], INT),
         "paco_last_kernel_ms": ([P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_char_p)], INT),
@@ -300,6 +302,35 @@ def paco_lcs_poll(ctx: Context, ticket: int, n: int = 0, m: int = 0, want_bounda
         return None
     _check(rc, ctx)
     return int(L.value), row, col
+
+
+def paco_lcs_submit_many(ctx: Context, a_cat, a_off, b_cat, b_off):
+    """Submit len(a_off)-1 length-only requests (host arrays) in one call;
+    returns their tickets (uint64 array)."""
+    import numpy as np
+    a_cat = np.ascontiguousarray(a_cat, dtype=np.uint8)
+    b_cat = np.ascontiguousarray(b_cat, dtype=np.uint8)
+    a_off = np.ascontiguousarray(a_off, dtype=np.int64)
+    b_off = np.ascontiguousarray(b_off, dtype=np.int64)
+    count = a_off.size - 1
+    t = np.zeros(max(count, 1), dtype=np.uint64)
+    taken = ctypes.c_int64(0)
+    vp = lambda x: x.ctypes.data_as(ctypes.c_void_p)
+    _check(load().paco_lcs_submit_many(ctx.handle, vp(a_cat), vp(a_off), vp(b_cat), vp(b_off), count, vp(t),
+                                       ctypes.byref(taken)), ctx)
+    return t[:count]
+
+
+def paco_lcs_poll_many(ctx: Context, tickets):
+    """Poll length-only tickets: returns (status, lengths) int32 arrays;
+    status PACO_PENDING for those still running (finished ones are released)."""
+    import numpy as np
+    tickets = np.ascontiguousarray(tickets, dtype=np.uint64)
+    st = np.empty(max(tickets.size, 1), dtype=np.int32)
+    ln = np.zeros(max(tickets.size, 1), dtype=np.int32)
+    vp = lambda x: x.ctypes.data_as(ctypes.c_void_p)
+    _check(load().paco_lcs_poll_many(ctx.handle, vp(tickets), tickets.size, vp(ln), vp(st), None), ctx)
+    return st[:tickets.size], ln[:tickets.size]
 
 
 def paco_serve_get_stats(ctx: Context) -> dict:

@@ -529,6 +529,9 @@ struct BatchState {
     int *err_ptr = nullptr;
     // device copies of the current layout
     DevBuf jobs, pjobs, cjobs, hbuf, rbits, bbits, coffs, epoch;
+    // pinned staging of the layout tables (stream-ordered uploads)
+    void *h_stage = nullptr;
+    size_t h_stage_cap = 0;
     uint64_t layout_key = 0;
     int64_t njobs = 0, npjobs = 0, ncjobs = 0;
     // captured graph of the whole batch step
@@ -609,6 +612,7 @@ void batch_state_free(BatchState *B) {
     if (B->exec) cudaGraphExecDestroy(B->exec);
     for (DevBuf *b : {&B->jobs, &B->pjobs, &B->cjobs, &B->hbuf, &B->rbits, &B->bbits, &B->coffs, &B->epoch})
         if (b->ptr) cudaFree(b->ptr);
+    if (B->h_stage) cudaFreeHost(B->h_stage);
     delete B;
 }
 
@@ -631,23 +635,65 @@ int run_batch(paco_ctx *ctx, BatchState *B, const uint8_t *a_cat, const int64_t 
     if (key != B->layout_key) {
         Layout lay;
         plan_batch(npairs, h_a_off, h_b_off, rows_cat != nullptr, cols_cat != nullptr, h_row_off, h_col_off, lay);
-        if ((rc = ensure_bytes(ctx, B->jobs, lay.jobs.size() * sizeof(SegJob) + 64)) != PACO_OK) return rc;
-        if ((rc = ensure_bytes(ctx, B->pjobs, lay.pjobs.size() * sizeof(PrefixJob) + 64)) != PACO_OK) return rc;
-        if ((rc = ensure_bytes(ctx, B->cjobs, lay.cjobs.size() * sizeof(ColJob) + 64)) != PACO_OK) return rc;
-        if ((rc = ensure_bytes(ctx, B->coffs, (size_t)lay.cwords * 4 + 64)) != PACO_OK) return rc;
-        if ((rc = ensure_bytes(ctx, B->hbuf, (size_t)lay.hwords * 8 + 64)) != PACO_OK) return rc;
-        if ((rc = ensure_bytes(ctx, B->rbits, (size_t)lay.rwords * 4 + 64)) != PACO_OK) return rc;
-        if ((rc = ensure_bytes(ctx, B->bbits, (size_t)lay.bwords * 4 + 64)) != PACO_OK) return rc;
-        if ((rc = ensure_bytes(ctx, B->epoch, 64)) != PACO_OK) return rc;
-        cudaError_t e = cudaSuccess;
-        if (!lay.jobs.empty())
-            e = cudaMemcpy(B->jobs.ptr, lay.jobs.data(), lay.jobs.size() * sizeof(SegJob), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess && !lay.pjobs.empty())
-            e = cudaMemcpy(B->pjobs.ptr, lay.pjobs.data(), lay.pjobs.size() * sizeof(PrefixJob),
-                           cudaMemcpyHostToDevice);
-        if (e == cudaSuccess && !lay.cjobs.empty())
-            e = cudaMemcpy(B->cjobs.ptr, lay.cjobs.data(), lay.cjobs.size() * sizeof(ColJob), cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) return set_cuda_error(ctx, e, "upload batch layout");
+        const size_t bj = lay.jobs.size() * sizeof(SegJob), bp = lay.pjobs.size() * sizeof(PrefixJob),
+                     bc = lay.cjobs.size() * sizeof(ColJob);
+        if (B != ctx->batch) {
+            // a serving slot: its buffers are used by its own stream only, so
+            // they grow stream-ordered (no device-wide synchronisation) and
+            // the layout goes up from pinned staging asynchronously; the slot
+            // is reused only after its previous micro-batch has completed
+            auto grow = [&](DevBuf &d, size_t need, bool zero) -> int {
+                if (d.bytes >= need) return PACO_OK;
+                if (d.ptr) cudaFreeAsync(d.ptr, st);
+                d.ptr = nullptr;
+                d.bytes = 0;
+                const size_t want = std::max(need * 2, (size_t)4096);
+                if (cudaMallocAsync(&d.ptr, want, st) != cudaSuccess) return PACO_ENOMEM;
+                d.bytes = want;
+                if (zero && cudaMemsetAsync(d.ptr, 0, want, st) != cudaSuccess) return PACO_EDEVICE;
+                return PACO_OK;
+            };
+            if ((rc = grow(B->jobs, bj + 64, false)) != PACO_OK || (rc = grow(B->pjobs, bp + 64, false)) != PACO_OK ||
+                (rc = grow(B->cjobs, bc + 64, false)) != PACO_OK ||
+                (rc = grow(B->coffs, (size_t)lay.cwords * 4 + 64, false)) != PACO_OK ||
+                (rc = grow(B->hbuf, (size_t)lay.hwords * 8 + 64, true)) != PACO_OK ||
+                (rc = grow(B->rbits, (size_t)lay.rwords * 4 + 64, false)) != PACO_OK ||
+                (rc = grow(B->bbits, (size_t)lay.bwords * 4 + 64, false)) != PACO_OK ||
+                (rc = grow(B->epoch, 64, true)) != PACO_OK)
+                return rc;
+            const size_t need = bj + bp + bc + 64;
+            if (B->h_stage_cap < need) {
+                if (B->h_stage) cudaFreeHost(B->h_stage);
+                B->h_stage = nullptr;
+                B->h_stage_cap = 0;
+                if (cudaMallocHost(&B->h_stage, need * 2) != cudaSuccess) return PACO_ENOMEM;
+                B->h_stage_cap = need * 2;
+            }
+            unsigned char *hs = (unsigned char *)B->h_stage;
+            if (bj) std::memcpy(hs, lay.jobs.data(), bj);
+            if (bp) std::memcpy(hs + bj, lay.pjobs.data(), bp);
+            if (bc) std::memcpy(hs + bj + bp, lay.cjobs.data(), bc);
+            cudaError_t e = cudaSuccess;
+            if (bj) e = cudaMemcpyAsync(B->jobs.ptr, hs, bj, cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess && bp) e = cudaMemcpyAsync(B->pjobs.ptr, hs + bj, bp, cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess && bc)
+                e = cudaMemcpyAsync(B->cjobs.ptr, hs + bj + bp, bc, cudaMemcpyHostToDevice, st);
+            if (e != cudaSuccess) return set_cuda_error(ctx, e, "upload batch layout");
+        } else {
+            if ((rc = ensure_bytes(ctx, B->jobs, bj + 64)) != PACO_OK) return rc;
+            if ((rc = ensure_bytes(ctx, B->pjobs, bp + 64)) != PACO_OK) return rc;
+            if ((rc = ensure_bytes(ctx, B->cjobs, bc + 64)) != PACO_OK) return rc;
+            if ((rc = ensure_bytes(ctx, B->coffs, (size_t)lay.cwords * 4 + 64)) != PACO_OK) return rc;
+            if ((rc = ensure_bytes(ctx, B->hbuf, (size_t)lay.hwords * 8 + 64)) != PACO_OK) return rc;
+            if ((rc = ensure_bytes(ctx, B->rbits, (size_t)lay.rwords * 4 + 64)) != PACO_OK) return rc;
+            if ((rc = ensure_bytes(ctx, B->bbits, (size_t)lay.bwords * 4 + 64)) != PACO_OK) return rc;
+            if ((rc = ensure_bytes(ctx, B->epoch, 64)) != PACO_OK) return rc;
+            cudaError_t e = cudaSuccess;
+            if (bj) e = cudaMemcpy(B->jobs.ptr, lay.jobs.data(), bj, cudaMemcpyHostToDevice);
+            if (e == cudaSuccess && bp) e = cudaMemcpy(B->pjobs.ptr, lay.pjobs.data(), bp, cudaMemcpyHostToDevice);
+            if (e == cudaSuccess && bc) e = cudaMemcpy(B->cjobs.ptr, lay.cjobs.data(), bc, cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) return set_cuda_error(ctx, e, "upload batch layout");
+        }
         B->ncjobs = (int64_t)lay.cjobs.size();
         B->njobs = (int64_t)lay.jobs.size();
         B->npjobs = (int64_t)lay.pjobs.size();

@@ -31,7 +31,10 @@ namespace {
 constexpr int kStreams = 4;
 constexpr size_t kMaxQueued = 1u << 20;
 constexpr int32_t kMaxBatchPairs = 8192;
-constexpr int64_t kMaxBatchCells = 2000000000LL;  // ~10-40 ms of work per micro-batch
+// Up to ~0.5 ms of device work per micro-batch at the batch kernel's rate:
+// small enough for four to overlap, large enough to amortise each
+// micro-batch's host work (layout, copies, launches).
+constexpr int64_t kMaxBatchCells = 20000000000LL;
 
 enum ReqState { kQueued, kRunning, kDone };
 
@@ -172,7 +175,7 @@ int launch_slot(ServeEngine *E, Slot &S) {
     int rc = run_batch(E->ctx, S.B, (const uint8_t *)S.a.ptr, S.a_off.data(), (const uint8_t *)S.b.ptr,
                        S.b_off.data(), np, (int32_t *)S.len.ptr, any_want ? (int32_t *)S.rows.ptr : nullptr,
                        S.row_off.data(), any_want ? (int32_t *)S.cols.ptr : nullptr, S.col_off.data(), S.stream,
-                       false, 4, E->ctx->opt_alphabet);
+                       false, 0, E->ctx->opt_alphabet);
     if (rc != PACO_OK) return rc;
     e = cudaMemcpyAsync(S.h_len, S.len.ptr, (size_t)np * 4, cudaMemcpyDeviceToHost, S.stream);
     if (e == cudaSuccess && any_want)
@@ -357,6 +360,88 @@ int paco_lcs_submit(paco_ctx *ctx, const uint8_t *a, int64_t n, const uint8_t *b
         E->stats.queued_now = E->queue.size();
     }
     E->cv.notify_one();
+    return PACO_OK;
+}
+
+int paco_lcs_submit_many(paco_ctx *ctx, const uint8_t *a_cat, const int64_t *a_off, const uint8_t *b_cat,
+                         const int64_t *b_off, int64_t count, uint64_t *tickets, int64_t *n_submitted) {
+    if (n_submitted) *n_submitted = 0;
+    if (!ctx || count < 0 || (count > 0 && (!a_off || !b_off || !tickets))) return PACO_EINVAL;
+    for (int64_t k = 0; k < count; ++k) {
+        const int64_t n = a_off[k + 1] - a_off[k], m = b_off[k + 1] - b_off[k];
+        if (n < 0 || m < 0 || n > 0x7fffffffLL || m > 0x7fffffffLL) return PACO_EINVAL;
+        if ((n > 0 && !a_cat) || (m > 0 && !b_cat)) return PACO_EINVAL;
+    }
+    int rc = PACO_OK;
+    paco::ServeEngine *E;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        cudaSetDevice(ctx->device);
+        E = paco::serve_get(ctx, &rc);
+    }
+    if (!E || rc != PACO_OK) return rc;
+    // copy the strings outside the engine lock
+    std::vector<std::unique_ptr<paco::Request>> rs;
+    rs.reserve((size_t)count);
+    for (int64_t k = 0; k < count; ++k) {
+        const int64_t n = a_off[k + 1] - a_off[k], m = b_off[k + 1] - b_off[k];
+        auto r = std::make_unique<paco::Request>();
+        r->a.assign(a_cat + a_off[k], a_cat + a_off[k] + n);
+        r->b.assign(b_cat + b_off[k], b_cat + b_off[k] + m);
+        r->want = false;
+        r->bytes = paco::request_bytes(n, m, false);
+        rs.push_back(std::move(r));
+    }
+    int64_t taken = 0;
+    rc = PACO_OK;
+    {
+        std::lock_guard<std::mutex> lk(E->mu);
+        for (auto &r : rs) {
+            if (r->bytes > E->budget || E->queue.size() >= paco::kMaxQueued) {
+                rc = PACO_EBUSY;
+                break;
+            }
+            r->ticket = E->next_ticket++;
+            tickets[taken++] = r->ticket;
+            E->queue.push_back(r.get());
+            E->all.emplace(r->ticket, std::move(r));
+            E->stats.submitted += 1;
+        }
+        E->stats.queued_now = E->queue.size();
+    }
+    if (n_submitted) *n_submitted = taken;
+    if (taken) E->cv.notify_one();
+    return rc;
+}
+
+int paco_lcs_poll_many(paco_ctx *ctx, const uint64_t *tickets, int64_t count, int32_t *len, int32_t *status,
+                       int64_t *n_done) {
+    if (n_done) *n_done = 0;
+    if (!ctx || count < 0 || (count > 0 && (!tickets || !len || !status))) return PACO_EINVAL;
+    paco::ServeEngine *E = ctx->serve;
+    if (!E) {
+        for (int64_t k = 0; k < count; ++k) status[k] = PACO_ENOTFOUND;
+        return PACO_OK;
+    }
+    int64_t done = 0;
+    std::lock_guard<std::mutex> lk(E->mu);
+    for (int64_t k = 0; k < count; ++k) {
+        auto it = E->all.find(tickets[k]);
+        if (it == E->all.end()) {
+            status[k] = PACO_ENOTFOUND;
+            continue;
+        }
+        paco::Request *r = it->second.get();
+        if (r->state != paco::kDone) {
+            status[k] = PACO_PENDING;
+            continue;
+        }
+        status[k] = r->status;
+        len[k] = r->status == PACO_OK ? r->len : 0;
+        E->all.erase(it);
+        ++done;
+    }
+    if (n_done) *n_done = done;
     return PACO_OK;
 }
 

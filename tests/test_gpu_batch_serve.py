@@ -213,6 +213,30 @@ def test_serve_alone_equals_in_mix(ctx):
     assert np.array_equal(alone[1], mixed[1]) and np.array_equal(alone[2], mixed[2])
 
 
+def test_serve_submit_many_and_poll_many(ctx):
+    """Batched submission and polling give the oracle's lengths, release
+    each ticket once, and report unknown tickets."""
+    A, B = _mixed_pairs(71, 90, LENS + [4000])
+    a_cat, a_off = _cat(A)
+    b_cat, b_off = _cat(B)
+    t = P.paco_lcs_submit_many(ctx, a_cat, a_off, b_cat, b_off)
+    assert t.size == 90 and np.unique(t).size == 90
+    got = np.full(90, -1, dtype=np.int64)
+    t0 = time.time()
+    while (got < 0).any():
+        idx = np.nonzero(got < 0)[0]
+        st, ln = P.paco_lcs_poll_many(ctx, t[idx])
+        assert np.all((st == P.PACO_OK) | (st == P.PACO_PENDING))
+        fin = st == P.PACO_OK
+        got[idx[fin]] = ln[fin]
+        assert time.time() - t0 < 120
+        time.sleep(0.0005)
+    for k in range(90):
+        assert got[k] == oracle.lcs(A[k], B[k])[0], k
+    st, _ = P.paco_lcs_poll_many(ctx, t[:3])
+    assert np.all(st == P.PACO_ENOTFOUND)
+
+
 def test_serve_budget_and_tickets():
     c = P.Context(0, mem_budget_bytes=1 << 20)
     try:
