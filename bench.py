@@ -512,13 +512,47 @@ def run_serve_bench(args):
     ctx.close()
 
 
+def run_recover_bench(args):
+    """One longest common subsequence of the 131072-square mutated pair
+    (Hirschberg levels on the batch engine): time per recovery, reported as
+    n*m / time beside the pair path's length-only figure."""
+    import torch
+    import paper_2011_01441_gb300 as P
+    P.load()
+    ctx = P.Context(0)
+    pair = W.single_mutated()
+    da, db = torch.from_numpy(pair.a).cuda(), torch.from_numpy(pair.b).cuda()
+    for _ in range(max(1, args.warmup)):
+        ai, bj = P.paco_lcs_subsequence(ctx, da, db)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        ai, bj = P.paco_lcs_subsequence(ctx, da, db)
+        torch.cuda.synchronize()
+        ts.append(time.perf_counter() - t0)
+    L = int(P.paco_lcs_length(ctx, da, db).item())
+    a_np, b_np = ai.cpu().numpy(), bj.cpu().numpy()
+    valid = (a_np.size == L and bool(np.all(np.diff(a_np) > 0)) and bool(np.all(np.diff(b_np) > 0))
+             and bool(np.array_equal(pair.a[a_np], pair.b[b_np])))
+    med = statistics.median(ts)
+    cells = float(pair.a.size) * pair.b.size
+    line = {"metric": METRIC, "value": cells / med / 1e9, "unit": "GCUPS (n*m per recovery)", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": med * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "LCS recovery, pair 131072x131072 sigma=20 mutated (seed 2)",
+                       "method": "Hirschberg levels, each one batch launch", "L": L, "valid": valid}}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="mutated", choices=["mutated", "small", "skinny", "batch", "serve"])
+    ap.add_argument("--config", default="mutated", choices=["mutated", "small", "skinny", "batch", "serve", "recover"])
     ap.add_argument("--requests", type=int, default=3000, help="serving: requests taken from the stream")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="batch: skip the one-pair-per-launch comparison")
@@ -529,6 +563,8 @@ def main():
         run_batch_bench(args)
     elif args.config == "serve":
         run_serve_bench(args)
+    elif args.config == "recover":
+        run_recover_bench(args)
     else:
         run_gpu(args)
 

@@ -244,6 +244,26 @@ typedef struct paco_serve_stats {
 } paco_serve_stats;
 int paco_serve_get_stats(paco_ctx *ctx, paco_serve_stats *out);
 
+/* ---- subsequence recovery -------------------------------------------- */
+
+/* One longest common subsequence of a (n, DEVICE) and b (m, DEVICE), not only
+ * its length: the paper computes the length and names recovering the
+ * subsequence as the harder variant (Sec. "PACO LCS", footnote to Eq. (1)).
+ * Recovery is Hirschberg's linear-space divide and conquer (CACM 18(6),
+ * 1975): each level cuts every subproblem at its middle row and finds the
+ * best column of the cut from the forward bottom row of the upper half and
+ * the bottom row of the reversed lower half, all subproblems of a level in
+ * one batch launch; about 2 n m cells in all, O(n + m) device memory.
+ * Output: *d_len = L, and DEVICE d_ai[0, L), d_bj[0, L) (capacity min(n, m))
+ * with a[d_ai[k]] == b[d_bj[k]], both strictly increasing.  Which of the
+ * longest subsequences is returned is fixed (the smallest best column at
+ * every cut, the first equal column for a single row) but not part of the
+ * contract.  Synchronous: returns when the result is in the buffers (the
+ * call synchronises `stream` once per level); like every call on a context,
+ * order it with the context's other calls. */
+int paco_lcs_subsequence(paco_ctx *ctx, const uint8_t *a, int64_t n, const uint8_t *b, int64_t m,
+                         int32_t *d_ai, int32_t *d_bj, int32_t *d_len, void *stream);
+
 /* ---- measurement helpers ---------------------------------------------- */
 
 /* Device microbenchmark of the 32-bit integer ALU issue rate used as the

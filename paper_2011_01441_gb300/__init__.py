@@ -90,6 +90,7 @@ def load():
         "paco_lcs_submit": ([P, P, I64, P, I64, INT, ctypes.POINTER(ctypes.c_uint64)], INT),
         "paco_lcs_poll": ([P, ctypes.c_uint64, P, P, P], INT),
         "paco_lcs_submit_many": ([P, P, P, P, P, I64, P, P], INT),
+        "paco_lcs_subsequence": ([P, P, I64, P, I64, P, P, P, P], INT),
         "paco_lcs_poll_many": ([P, P, I64, P, P, P], INT),
         "paco_serve_get_stats": ([P, ctypes.POINTER(PacoServeStats)], INT),
         "paco_measure_int_peak": ([P, INT, ctypes.POINTER(ctypes.c_double), P], INT),
@@ -331,6 +332,22 @@ def paco_lcs_poll_many(ctx: Context, tickets):
     vp = lambda x: x.ctypes.data_as(ctypes.c_void_p)
     _check(load().paco_lcs_poll_many(ctx.handle, vp(tickets), tickets.size, vp(ln), vp(st), None), ctx)
     return st[:tickets.size], ln[:tickets.size]
+
+
+def paco_lcs_subsequence(ctx: Context, a, b, stream=None):
+    """One LCS of device uint8 tensors a, b: returns (ai, bj) int32 device
+    tensors of length L with a[ai] == b[bj], both strictly increasing."""
+    import torch
+    a, b = _u8(a, "a"), _u8(b, "b")
+    n, m = a.numel(), b.numel()
+    cap = max(1, min(n, m))
+    ai = torch.empty(cap, dtype=torch.int32, device=a.device)
+    bj = torch.empty(cap, dtype=torch.int32, device=a.device)
+    ln = torch.zeros(1, dtype=torch.int32, device=a.device)
+    _check(load().paco_lcs_subsequence(ctx.handle, _ptr(a), n, _ptr(b), m, _ptr(ai), _ptr(bj), _ptr(ln),
+                                       _stream(stream)), ctx)
+    L = int(ln.item())
+    return ai[:L], bj[:L]
 
 
 def paco_serve_get_stats(ctx: Context) -> dict:

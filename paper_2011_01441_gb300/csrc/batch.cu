@@ -545,6 +545,8 @@ struct BatchState {
 void batch_release(paco_ctx *ctx) {
     batch_state_free(ctx->batch);
     ctx->batch = nullptr;
+    batch_state_free(ctx->recover);
+    ctx->recover = nullptr;
 }
 
 namespace {

@@ -51,6 +51,7 @@ struct paco_ctx {
     cudaStream_t own_stream = nullptr;
     std::map<std::tuple<int64_t, int64_t, int, int, int, int>, std::unique_ptr<paco::CachedPairPlan>> plans;
     paco::BatchState *batch = nullptr;
+    paco::BatchState *recover = nullptr;  // the subsequence recovery's batch engine state
     paco::ServeEngine *serve = nullptr;
 
     int *err_ptr() { return (int *)small.ptr; }
