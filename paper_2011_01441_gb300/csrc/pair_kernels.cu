@@ -326,9 +326,10 @@ __global__ void __launch_bounds__(256, 1) k_pair_bp(const PairArgs P) {
         bool ok = true;
         int cons_seen = 0;  // warps w > 0 downstream: last consumption count read
         const uint32_t ring_tag0 = 1;
-        for (int64_t u = 0; u < nouter; ++u) {
+        // 32-bit word and column indices in the loop (S < 2^31 columns)
+        for (int u = 0; u < (int)nouter; ++u) {
             // inputs of this word: column offsets up to word u+1, the input carry word u
-            const int need_c = (int)min(u + 2, nvwords);
+            const int need_c = (int)min((int64_t)u + 2, nvwords);
             const int need_s = (w == 0 && u < nwords) ? (int)(u + 1) : 0;
             const uint64_t *rw = (w > 0 && u < nwords) ? ring_in + (u % kRing) : nullptr;
             uint32_t srcw = 0;
@@ -352,9 +353,9 @@ __global__ void __launch_bounds__(256, 1) k_pair_bp(const PairArgs P) {
                 else srcw = (uint32_t)rv;
             }
             if (lane == 0) st_release_shared(cons0 + 4u * (uint32_t)w, (int)(u + 1));
-            const int64_t ubase = u * K;
+            const int ubase = u * K;
             // this lane's column of step 0 (upper word) and its place in the ring
-            const int64_t c0 = u * 32 - (int64_t)kSk * C * lane;
+            const int c0 = u * 32 - kSk * C * lane;
             const uint32_t cbase = col_ring + (uint32_t)(((c0 >> 5) & (R - 1)) * 128) + (uint32_t)((c0 & 31) * 4);
             auto offs_at = [&](uint32_t addr, uint32_t (&o)[C]) {
                 if constexpr (C == 2) {
@@ -426,7 +427,7 @@ __global__ void __launch_bounds__(256, 1) k_pair_bp(const PairArgs P) {
                     onext[jj] = onext2[jj];
                 }
                 if (i == kFlushStep) {  // lane 31 completes word wq (a predicated store)
-                    const int64_t wq = ((ubase + i - kLag) * C) >> 5;
+                    const int wq = ((ubase + i - kLag) * C) >> 5;
                     const bool fl = lane == 31 && wq >= 0 && wq < nwords;
                     if (w + 1 < W) {
                         // the next warp has consumed up to cons_seen: wait only when
