@@ -10,6 +10,10 @@ caller-given first row/column, see `lcs_oracle.c`):
 * `lcs(a, b, top=None, left=None)` -> (L, bottom_row[m+1], right_col[n+1])
 * `lcs_table(a, b, top=None, left=None)` -> full (n+1) x (m+1) table
 * `lcs_batch(a_cat, a_off, b_cat, b_off, threads)` -> per-pair L, rows, cols
+* `lcs_bitpar(a, b)` -> (L, bottom_row, right_col) by an independent method
+  (the bit-vector LCS of Allison & Dix / Hyyro, `lcs_bitpar.c`), zero
+  boundaries only: a cross-check of the DP on large inputs, not the
+  definition
 
 Pins that tie it to something other than itself live in
 `tests/test_oracle_pins.py` (brute-force enumeration, indel distance,
@@ -26,6 +30,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lcs_oracle.c")
+_SRC_BITPAR = os.path.join(_HERE, "lcs_bitpar.c")
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -33,10 +38,11 @@ _lib = None
 
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (plain C, -O2, no vector intrinsics)."""
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_BITPAR))
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < newest:
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-pthread",
-                               _SRC, "-o", tmp])
+                               _SRC, _SRC_BITPAR, "-o", tmp])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -55,6 +61,8 @@ def _load():
             lib.oracle_lcs_table.restype = ctypes.c_int
             lib.oracle_lcs_batch.argtypes = [P, P, P, P, I64, P, P, P, P, P, ctypes.c_int]
             lib.oracle_lcs_batch.restype = ctypes.c_int
+            lib.oracle_lcs_bitpar.argtypes = [P, I64, P, I64, P, P, P]
+            lib.oracle_lcs_bitpar.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -134,3 +142,19 @@ def lcs_batch(a_cat, a_off, b_cat, b_off, threads=None, boundaries=True):
     if rc != 0:
         raise ValueError(f"oracle_lcs_batch failed ({rc})")
     return L, rows, row_off, cols, col_off
+
+
+def lcs_bitpar(a, b):
+    """(L, bottom_row[m+1], right_col[n+1]) by the bit-vector method."""
+    a = _u8(a)
+    b = _u8(b)
+    n, m = a.size, b.size
+    L = ctypes.c_int32(0)
+    row = np.zeros(m + 1, dtype=np.int32)
+    col = np.zeros(n + 1, dtype=np.int32)
+    vp = lambda x: x.ctypes.data_as(ctypes.c_void_p)
+    rc = _load().oracle_lcs_bitpar(vp(a) if n else None, n, vp(b) if m else None, m, ctypes.byref(L),
+                                   vp(row), vp(col))
+    if rc != 0:
+        raise RuntimeError(f"oracle_lcs_bitpar failed ({rc})")
+    return int(L.value), row, col

@@ -10,6 +10,7 @@ import pytest
 
 import oracle
 from oracle import brute
+from paper_2011_01441_gb300 import workloads as W
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -223,3 +224,38 @@ def test_planted_mistakes_are_caught():
                 caught = True
                 break
         assert caught, kind
+
+
+# ---- the independent bit-vector routine (Allison & Dix / Hyyro) against the DP ----
+
+def test_bitpar_against_bruteforce_exhaustive_binary():
+    for n in range(0, 6):
+        for m in range(0, 6):
+            for x in range(1 << n):
+                a = [(x >> k) & 1 for k in range(n)]
+                for y in range(0, 1 << m, 3):
+                    b = [(y >> k) & 1 for k in range(m)]
+                    L, row, col = oracle.lcs_bitpar(np.array(a, np.uint8), np.array(b, np.uint8))
+                    assert L == brute.lcs_brute(a, b)
+                    assert list(row) == brute.bottom_row_brute(a, b)
+                    assert list(col) == brute.right_col_brute(a, b)
+
+
+@pytest.mark.parametrize("n,m,sigma", [(0, 7, 4), (7, 0, 4), (1, 1, 2), (63, 64, 4), (64, 65, 4), (65, 63, 2),
+                                       (127, 128, 20), (1000, 3000, 4), (3001, 999, 256), (4096, 4096, 4)])
+def test_bitpar_equals_dp(n, m, sigma):
+    a = W.symbols(n + 11 * m, 0, n, sigma)
+    b = W.symbols(n + 11 * m, 1, m, sigma)
+    d = oracle.lcs(a, b)
+    t = oracle.lcs_bitpar(a, b)
+    assert d[0] == t[0]
+    assert np.array_equal(d[1], t[1]) and np.array_equal(d[2], t[2])
+
+
+def test_bitpar_equals_dp_mutated_20000():
+    """Two independent CPU methods agree on a 20000-square mutated pair."""
+    a = W.symbols(12, 0, 20000, 20)
+    b = W.mutate_rate(a, 20, 0.15, 12, 1)
+    d = oracle.lcs(a, b)
+    t = oracle.lcs_bitpar(a, b)
+    assert d[0] == t[0] and np.array_equal(d[1], t[1]) and np.array_equal(d[2], t[2])
