@@ -124,7 +124,6 @@ extern "C" int paco_lcs_boundaries_static(const uint8_t *a, int64_t n, const uin
     P.b = kb;
     P.L = L;
     P.S = S;
-    P.nchunks = (S + pl.C - 1) / pl.C;
     P.nwords = nwords;
     P.hstride = hstride;
     P.strip_row0 = nullptr;

@@ -16,30 +16,27 @@ constexpr int kMaxSigma = 256;
 // Slots of the shared-memory ring that hands carry words from one warp of a
 // CTA strip to the next.
 constexpr int kRing = 32;
-// Rows one lane holds (bit 31 of its word is the carry slot) and one warp holds.
-constexpr int kLaneRowsH = 31;
-constexpr int kWarpRows = 31 * 32;
 
 // ---------------------------------------------------------------------------
 // Single pair, bit-parallel strip pipeline.
 //
 // The table is processed with its rows along bits: row string `a` (length
 // L), column string `b` (length S).  Rows are cut into `nstrips` CTA strips
-// (balanced 32-row granules); CTA strip s is W warps x 32 lanes x 32 rows.
-// Columns are cut into chunks of C columns; a lane hands the C carry bits of
-// a chunk (the horizontal steps of the table at the lane's last row) to the
-// next lane.  Between CTA strips, the carries of the strip's last row travel
-// through `hbuf`, tagged with the launch epoch so a consumer can tell a
-// published word from a stale one without a separate flag.
+// (balanced granules of one lane's rows, 31 x words per lane); CTA strip s
+// is W warps x 32 lanes x (31 x words per lane) rows.  Columns are cut into
+// chunks of C columns; a lane hands the C carry bits of a chunk (the
+// horizontal steps of the table at the lane's last row) to the next lane.
+// Between CTA strips, the carries of the strip's last row travel through
+// `hbuf`, tagged with the launch epoch so a consumer can tell a published
+// word from a stale one without a separate flag.
 // ---------------------------------------------------------------------------
 struct PairArgs {
     const uint8_t *a;            // row string (bits), length L
     const uint8_t *b;            // column string (streamed), length S
     int64_t L, S;
-    int64_t nchunks;             // ceil(S / C)
     int64_t nwords;              // ceil(S / 32): words per carry row
     int64_t hstride;             // words between carry rows (nwords rounded up to even)
-    const int64_t *strip_row0;   // nstrips+1 row offsets (multiples of 31, last = L), or NULL:
+    const int64_t *strip_row0;   // nstrips+1 row offsets (multiples of 31 * wpl, last = L), or NULL:
     int64_t granules;            //   then strip s starts at 31*wpl*(s*(granules/nstrips) + min(s, granules%nstrips))
     int nstrips;
     int sigma;                   // match-table rows (symbols must be < sigma)

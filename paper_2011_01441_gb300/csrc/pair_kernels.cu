@@ -319,8 +319,8 @@ __global__ void __launch_bounds__(256, 1) k_pair_bp(const PairArgs P) {
         }
         uint32_t cin_cur = 0;   // the lane above's carry word for this step (sent two steps ago)
         uint32_t cin_nxt = 0;   // ... and for the next step
-        uint32_t Mcur[C];       // steady state: the upper word's match words for this step
-        uint32_t onext[C];      // steady state: the next step's column offsets
+        uint32_t Mcur[C];       // the upper word's match words for this step
+        uint32_t onext[C];      // the next step's column offsets
         uint32_t oprev[C];      // two words: this step's offsets, for the lower word next step
         uint32_t Mlow[C];       // two words: the lower word's match words for this step
         bool ok = true;

@@ -111,7 +111,6 @@ int run_pair(paco_ctx *ctx, const uint8_t *a, int64_t n, const uint8_t *b, int64
     P.b = kb;
     P.L = L;
     P.S = S;
-    P.nchunks = (S + pl.C - 1) / pl.C;
     P.nwords = nwords;
     P.hstride = hstride;
     P.strip_row0 = (const int64_t *)cp->d_row0.ptr;
