@@ -11,9 +11,12 @@
 // column k with the largest sum (the smallest such column on ties) splits
 // the subproblem into (a[i0, h), b[j0, j0 + k)) and (a[h, i1), b[j0 + k, j1)).
 // All subproblems of one level go through the batch engine as one launch
-// (two pairs each); a one-row subproblem matches its row's symbol with the
-// first equal column, if any.  Every row of a ends in exactly one one-row
-// subproblem, so the matches, read in row order, are the subsequence.
+// (two pairs each).  A subproblem of at most 31 rows is solved directly by
+// one warp: a ballot over the rows gives each column's match word, one
+// bit-vector word per column (Allison & Dix / Hyyro, V' = (V + (V & M)) |
+// (V & ~M)) is stored, and one lane walks back from the corner.  Every row of
+// a ends in exactly one such subproblem, so the matched rows, read in order,
+// are the subsequence.
 #include "../../include/paco_lcs.h"
 #include "ctx.hpp"
 #include "paco_internal.hpp"
@@ -42,8 +45,8 @@ struct Split {       // one subproblem cut at its middle row
     int64_t w;       // columns of the subproblem
 };
 
-struct Leaf {        // a one-row subproblem
-    int64_t i, j0, j1;
+struct Base {        // a subproblem of at most 31 rows, solved by one warp
+    int64_t i0, i1, j0, j1;
 };
 
 __global__ void k_gather(const uint8_t *src, const Seg *segs, uint8_t *dst) {
@@ -78,24 +81,46 @@ __global__ void k_split_column(const int32_t *rows, const Split *sp, int64_t *k_
     }
 }
 
-// match[i] = the first column j in [j0, j1) with b[j] == a[i], or -1.
-__global__ void k_leaf_match(const uint8_t *a, const uint8_t *b, const Leaf *lv, int32_t *match) {
-    const Leaf L = lv[blockIdx.x];
-    const uint8_t c = a[L.i];
-    int first = 0x7fffffff;
-    for (int64_t j = L.j0 + threadIdx.x; j < L.j1; j += blockDim.x)
-        if (b[j] == c) {
-            first = min(first, (int)j);
-            break;  // later j of this thread are larger
+// One warp per base subproblem (h <= 31 rows, w columns, zero boundaries):
+// lane r holds a[i0 + r]; column j's match word is the ballot of the lanes
+// whose symbol equals b[j]; the warp keeps V (bit r clear = vertical step
+// below row r) and lane 0 stores V after each column in vs[j].  Then lane 0
+// walks back from (h, w): H(i, j) = zero bits of column j's V below row i.
+__global__ void k_base_lcs(const uint8_t *a, const uint8_t *b, const Base *bs, uint32_t *vs, int32_t *match) {
+    const Base B = bs[blockIdx.x];
+    const int lane = threadIdx.x;
+    const int h = (int)(B.i1 - B.i0);
+    const int64_t w = B.j1 - B.j0;
+    const int ar = lane < h ? (int)a[B.i0 + lane] : 1000;  // rows past h never match
+    uint32_t V = 0xffffffffu;
+    for (int64_t jb = 0; jb < w; jb += 32) {  // 32 column symbols per coalesced load
+        const int bl = jb + lane < w ? (int)b[B.j0 + jb + lane] : -1;
+        const int cnt = (int)min((int64_t)32, w - jb);
+        for (int jj = 0; jj < cnt; ++jj) {
+            const uint32_t M = __ballot_sync(0xffffffffu, ar == __shfl_sync(0xffffffffu, bl, jj));
+            V = (V + (V & M)) | (V & ~M);
+            if (lane == 0) vs[B.j0 + jb + jj] = V;
         }
-    __shared__ int red[32];
-    for (int o = 16; o > 0; o >>= 1) first = min(first, __shfl_down_sync(0xffffffffu, first, o));
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = first;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        first = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0x7fffffff;
-        for (int o = 16; o > 0; o >>= 1) first = min(first, __shfl_down_sync(0xffffffffu, first, o));
-        if (threadIdx.x == 0) match[L.i] = first == 0x7fffffff ? -1 : first;
+    }
+    __syncwarp();
+    if (lane != 0) return;
+    auto H = [&](int i, int64_t j) -> int {  // H[i][j] of the subproblem
+        if (i == 0 || j == 0) return 0;
+        const uint32_t v = vs[B.j0 + j - 1];
+        return __popc(~v & ((1u << i) - 1u));
+    };
+    int i = h;
+    int64_t j = w;
+    while (i > 0 && j > 0) {
+        if (a[B.i0 + i - 1] == b[B.j0 + j - 1]) {  // Eq. (1): a diagonal step
+            match[B.i0 + i - 1] = (int32_t)(B.j0 + j - 1);
+            --i;
+            --j;
+        } else if (H(i - 1, j) == H(i, j)) {
+            --i;
+        } else {
+            --j;
+        }
     }
 }
 
@@ -176,9 +201,9 @@ int run_subsequence(paco_ctx *ctx, const uint8_t *a, int64_t n, const uint8_t *b
                     int32_t *d_bj, int32_t *d_len, cudaStream_t st) {
     if (!ctx->recover) ctx->recover = batch_state_new(ctx->ticket_ptr(), ctx->err_ptr());
     if (!ctx->recover) return PACO_ENOMEM;
-    DevBuf match, seg_a, seg_b, acat, bcat, rows, lens, splits, kbuf, leaves, cnt;
+    DevBuf match, seg_a, seg_b, acat, bcat, rows, lens, splits, kbuf, bases, vstore, cnt;
     auto release = [&]() {
-        for (DevBuf *d : {&match, &seg_a, &seg_b, &acat, &bcat, &rows, &lens, &splits, &kbuf, &leaves, &cnt})
+        for (DevBuf *d : {&match, &seg_a, &seg_b, &acat, &bcat, &rows, &lens, &splits, &kbuf, &bases, &vstore, &cnt})
             if (d->ptr) cudaFreeAsync(d->ptr, st);
     };
     auto fail = [&](int rc) {
@@ -194,14 +219,13 @@ int run_subsequence(paco_ctx *ctx, const uint8_t *a, int64_t n, const uint8_t *b
     if (n > 0 && m > 0) cur.push_back({0, n, 0, m});
     std::vector<Seg> sa, sb;
     std::vector<Split> sp;
-    std::vector<Leaf> lf;
+    std::vector<Base> base;  // every subproblem of at most 31 rows, solved at the end
     std::vector<int64_t> a_off, b_off, row_off, kh;
     std::vector<Sub> cut;
     while (!cur.empty()) {
         sa.clear();
         sb.clear();
         sp.clear();
-        lf.clear();
         cut.clear();
         a_off.assign(1, 0);
         b_off.assign(1, 0);
@@ -210,8 +234,8 @@ int run_subsequence(paco_ctx *ctx, const uint8_t *a, int64_t n, const uint8_t *b
         for (const Sub &s : cur) {
             const int64_t h = s.i1 - s.i0, w = s.j1 - s.j0;
             if (h <= 0 || w <= 0) continue;
-            if (h == 1) {
-                lf.push_back({s.i0, s.j0, s.j1});
+            if (h <= 31) {
+                base.push_back({s.i0, s.i1, s.j0, s.j1});
                 continue;
             }
             const int64_t mid = s.i0 + h / 2;
@@ -231,11 +255,6 @@ int run_subsequence(paco_ctx *ctx, const uint8_t *a, int64_t n, const uint8_t *b
             row_off.push_back(rows_tot);
             rows_tot += w + 1;
             sp.push_back({row_off[row_off.size() - 2], row_off.back(), w});
-        }
-        if (!lf.empty()) {
-            if ((rc = upload(leaves, lf, st)) != PACO_OK) return fail(rc);
-            k_leaf_match<<<(unsigned)lf.size(), 128, 0, st>>>(a, b, (const Leaf *)leaves.ptr, (int32_t *)match.ptr);
-            if (cudaGetLastError() != cudaSuccess) return fail(PACO_EDEVICE);
         }
         if (cut.empty()) break;
         const int32_t np = (int32_t)(2 * cut.size());
@@ -276,6 +295,14 @@ int run_subsequence(paco_ctx *ctx, const uint8_t *a, int64_t n, const uint8_t *b
             next.push_back({mid, s.i1, col, s.j1});
         }
         cur.swap(next);
+    }
+    // the base subproblems (disjoint column ranges: one word per column of b)
+    if (!base.empty()) {
+        if ((rc = upload(bases, base, st)) != PACO_OK) return fail(rc);
+        if ((rc = grow(vstore, (size_t)std::max<int64_t>(m, 1) * 4, st)) != PACO_OK) return fail(rc);
+        k_base_lcs<<<(unsigned)base.size(), 32, 0, st>>>(a, b, (const Base *)bases.ptr, (uint32_t *)vstore.ptr,
+                                                        (int32_t *)match.ptr);
+        if (cudaGetLastError() != cudaSuccess) return fail(PACO_EDEVICE);
     }
     // compaction in row order
     const int64_t nb = (std::max<int64_t>(n, 1) + kCB - 1) / kCB;
