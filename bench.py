@@ -546,13 +546,65 @@ def run_recover_bench(args):
     ctx.close()
 
 
+def run_schedules_bench(args):
+    """The paper's comparison on one GB300: the 131072-square mutated pair
+    under the strip pipeline and under the PACO, PA and PO tile schedules
+    (all on the same warp kernel), with each schedule's critical path from
+    the planner in units of n*m/p."""
+    import torch
+    import paper_2011_01441_gb300 as P
+    P.load()
+    ctx = P.Context(0)
+    pair = W.single_mutated()
+    n, m = pair.a.size, pair.b.size
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    da, db = torch.from_numpy(pair.a).cuda(), torch.from_numpy(pair.b).cuda()
+    L_ref = None
+    rows = {}
+    for name, kind, base in (("strips (PACO p-way rows)", 0, 0), ("PACO tiles", P.TILES_PACO, 4),
+                             ("PACO tiles base 2", P.TILES_PACO, 2), ("PA p x p", P.TILES_PA, 4),
+                             ("PO 2-way D&C", P.TILES_PO, 16)):
+        ctx.set_option(P.OPT_TILES, kind)
+        ctx.set_option(P.OPT_TILE_BASE, base)
+        for _ in range(max(1, args.warmup)):
+            L, _, _ = P.paco_lcs_boundaries(ctx, da, db)
+        ctx.sync()
+        ks = []
+        for _ in range(args.steps):
+            P.paco_lcs_boundaries(ctx, da, db)
+            ctx.sync()
+            ks.append(P.paco_last_kernel_ms(ctx)[0])
+        Lv = int(L.item())
+        L_ref = Lv if L_ref is None else L_ref
+        crit = None
+        if kind:
+            t = P.paco_plan_tiles(n, m, sms, kind, base)
+            crit = t["critical_cells"] / (n * m / sms)
+            ntiles = len(t["tiles"])
+        else:
+            ntiles = P.paco_plan_pair(n, m, sms)["nstrips"]
+        med = statistics.median(ks)
+        rows[name] = {"kernel_ms": med, "gcups": n * m / (med * 1e-3) / 1e9, "tiles": ntiles,
+                      "critical_path_nm_over_p": crit, "L_matches": Lv == L_ref}
+    ctx.set_option(P.OPT_TILES, 0)
+    ctx.set_option(P.OPT_TILE_BASE, 0)
+    best = max(rows.values(), key=lambda r: r["gcups"])
+    line = {"metric": METRIC, "value": best["gcups"], "unit": "GCUPS", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "schedule comparison, pair 131072x131072 sigma=20 mutated (seed 2)", "p": sms},
+            "schedules": rows}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="mutated", choices=["mutated", "small", "skinny", "batch", "serve", "recover"])
+    ap.add_argument("--config", default="mutated", choices=["mutated", "small", "skinny", "batch", "serve", "recover", "schedules"])
     ap.add_argument("--requests", type=int, default=3000, help="serving: requests taken from the stream")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="batch: skip the one-pair-per-launch comparison")
@@ -565,6 +617,8 @@ def main():
         run_serve_bench(args)
     elif args.config == "recover":
         run_recover_bench(args)
+    elif args.config == "schedules":
+        run_schedules_bench(args)
     else:
         run_gpu(args)
 

@@ -109,6 +109,12 @@ enum paco_option {
     PACO_OPT_WORDS_PER_LANE = 9, /* single pair: 31-row words per lane, 1 or 2 (0 =
                                    planner); two words give each lane two
                                    dependency chains and halve the strips */
+    PACO_OPT_TILES = 10,        /* single pair: 0 = strip pipeline; 1, 2, 3 = the tile
+                                   schedules of include/paco_plan.h (PACO partition, PA
+                                   p x p blocks, PO divide and conquer) on the batch
+                                   kernel, for the paper's comparison; zero boundaries only */
+    PACO_OPT_TILE_BASE = 11,    /* tile schedules: smallest tile side in 31-row / 64-column
+                                   granules (0 = 4 for PACO, 16 for PO) */
     PACO_OPT_TEST_STALL = 100   /* tests only: make one strip wait on a flag
                                    nothing sets (exercises the bounded wait) */
 };

@@ -62,6 +62,21 @@ int paco_plan_pair(int64_t n, int64_t m, int32_t sms, int32_t chunk, int32_t war
                    int32_t schedule, int32_t words_per_lane, paco_pair_plan *out, int64_t *row0,
                    int64_t cap);
 
+/* Tile schedules for the comparison the paper runs (PACO against the
+ * processor-aware PA and the processor-oblivious PO divide and conquer),
+ * all on a grid of 31-row x 64-column granules, tiles at most 992 rows:
+ *   kind 1 = PACO: the partition above on the granule grid (base in granules);
+ *   kind 2 = PA: a p x p grid of blocks in anti-diagonal order;
+ *   kind 3 = PO: 2-way divide and conquer down to base x base granules, with
+ *            the fork-join order (X11; X12 and X21; X22) as dependencies.
+ * Writes up to `cap` tiles in execution order (label/owner unused: 0), the
+ * dependency CSR (dep_off[count+1], dep_idx up to cap_idx), the number of
+ * tiles and dependency entries, and the heaviest dependency path in cells
+ * (*critical_cells; the paper's critical-path measure).  Returns 0 or -1. */
+int paco_plan_tiles(int64_t n, int64_t m, int32_t p, int32_t kind, int64_t base, paco_tile *out,
+                    int64_t cap, int64_t *count, int64_t *dep_off, int64_t *dep_idx, int64_t cap_idx,
+                    int64_t *n_idx, int64_t *critical_cells);
+
 #ifdef __cplusplus
 }
 #endif

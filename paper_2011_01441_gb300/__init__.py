@@ -36,6 +36,8 @@ OPT_SCHEDULE = 6
 OPT_ALPHABET = 7
 OPT_BATCH_CHUNKS = 8
 OPT_WORDS_PER_LANE = 9
+OPT_TILES = 10
+OPT_TILE_BASE = 11
 OPT_TEST_STALL = 100
 
 _lib = None
@@ -98,6 +100,7 @@ def load():
         "paco_plan_partition": ([I64, I64, I32, I64, P, I64, ctypes.POINTER(I64)], INT),
         "paco_plan_partition_deps": ([I64, I64, I32, I64, P, P, I64, ctypes.POINTER(I64)], INT),
         "paco_plan_pair": ([I64, I64, I32, I32, I32, I32, I32, I32, ctypes.POINTER(PacoPairPlan), P, I64], INT),
+        "paco_plan_tiles": ([I64, I64, I32, I32, I64, P, I64, P, P, P, I64, P, P], INT),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -393,6 +396,26 @@ def paco_plan_partition_deps(n: int, m: int, p: int, base: int):
                                            idx.ctypes.data_as(ctypes.c_void_p), nidx.value,
                                            ctypes.byref(nidx)))
     return off, idx[:nidx.value]
+
+
+TILES_PACO, TILES_PA, TILES_PO = 1, 2, 3
+
+
+def paco_plan_tiles(n: int, m: int, p: int, kind: int, base: int):
+    """Tile schedule (kind TILES_PACO / TILES_PA / TILES_PO): returns dict with
+    tiles (list of dicts r0 r1 c0 c1), dep_off, dep_idx, critical_cells."""
+    import numpy as np
+    cnt, nidx, crit = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(load().paco_plan_tiles(n, m, p, kind, base, None, 0, ctypes.byref(cnt), None, None, 0,
+                                  ctypes.byref(nidx), ctypes.byref(crit)))
+    arr = (PacoTile * max(1, cnt.value))()
+    off = np.zeros(cnt.value + 1, dtype=np.int64)
+    idx = np.zeros(max(1, nidx.value), dtype=np.int64)
+    vp = lambda x: x.ctypes.data_as(ctypes.c_void_p)
+    _check(load().paco_plan_tiles(n, m, p, kind, base, arr, cnt.value, ctypes.byref(cnt), vp(off), vp(idx),
+                                  idx.size, ctypes.byref(nidx), ctypes.byref(crit)))
+    tiles = [{k: getattr(arr[i], k) for k in ("r0", "r1", "c0", "c1")} for i in range(cnt.value)]
+    return {"tiles": tiles, "dep_off": off, "dep_idx": idx[:nidx.value], "critical_cells": crit.value}
 
 
 def paco_plan_pair(n: int, m: int, sms: int, chunk=0, warps=0, orient=0, schedule=0, words_per_lane=0):

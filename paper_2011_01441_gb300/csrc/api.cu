@@ -170,6 +170,14 @@ int paco_ctx_set_option(paco_ctx *ctx, int option, int64_t value) {
             if (value < 0 || value > 2) return PACO_EINVAL;
             ctx->opt_wpl = (int)value;
             return PACO_OK;
+        case PACO_OPT_TILES:
+            if (value < 0 || value > 3) return PACO_EINVAL;
+            ctx->opt_tiles = (int)value;
+            return PACO_OK;
+        case PACO_OPT_TILE_BASE:
+            if (value < 0 || value > (1 << 20)) return PACO_EINVAL;
+            ctx->opt_tile_base = value;
+            return PACO_OK;
         case PACO_OPT_TEST_STALL:
             if (value < -1 || value > 0x7fffffff) return PACO_EINVAL;
             ctx->test_stall = (int)value;
@@ -190,6 +198,8 @@ int paco_ctx_get_option(paco_ctx *ctx, int option, int64_t *value) {
         case PACO_OPT_SCHEDULE: *value = ctx->opt_schedule; return PACO_OK;
         case PACO_OPT_ALPHABET: *value = ctx->opt_alphabet; return PACO_OK;
         case PACO_OPT_WORDS_PER_LANE: *value = ctx->opt_wpl; return PACO_OK;
+        case PACO_OPT_TILES: *value = ctx->opt_tiles; return PACO_OK;
+        case PACO_OPT_TILE_BASE: *value = ctx->opt_tile_base; return PACO_OK;
         case PACO_OPT_BATCH_CHUNKS: *value = ctx->last_batch_chunk; return PACO_OK;
         case PACO_OPT_TEST_STALL: *value = ctx->test_stall; return PACO_OK;
         default: return PACO_EINVAL;

@@ -29,7 +29,14 @@ namespace {
 
 using namespace dev;
 
-enum : uint32_t { kTransposed = 1u, kInGlobal = 2u, kOutGlobal = 4u, kFinal = 8u };
+enum : uint32_t {
+    kTransposed = 1u,
+    kInGlobal = 2u,   // top carries from tagged words of an earlier job
+    kOutGlobal = 4u,  // bottom carries to tagged words for a later job
+    kFinal = 8u,      // the pair's last segment: writes its length
+    kLeftIn = 16u,    // tiles: the first column's vertical steps from tagged lane words
+    kRightOut = 32u   // tiles: the last column's vertical steps to tagged lane words
+};
 // Size classes of the streamed side S (bits 8..9 of SegJob::flags); each
 // class runs with its own autotuned chunk width.
 constexpr int kClassShift = 8;
@@ -47,6 +54,12 @@ struct SegJob {
     int64_t hout;      // tagged output carry row (kOutGlobal)
     int64_t rword;     // first right-column lane word of the segment, or -1
     int64_t bword;     // first bottom-row step word of the pair (kFinal), or -1
+    int64_t vin;       // tiles: first tagged lane word of the left column (kLeftIn)
+    int64_t vout;      // tiles: first tagged lane word of the right column (kRightOut)
+    int32_t join0;     // tiles: jobs whose completion must be seen first (-1: none),
+    int32_t join1;     //   the fork-join order of a divide-and-conquer schedule
+    int32_t done;      // tiles: index of this job's completion flag, or -1
+    int32_t pad;
 };
 // (cols_off indexes the column-offset array, not the concatenation)
 
@@ -96,7 +109,40 @@ struct BatchArgs {
     int sigma;       // declared alphabet: symbols are < sigma
     int table_rows;  // rows of the per-warp match table: the zero row, then one per symbol
     int cls_chunk[4];  // chunk width of each size class
+    uint64_t *vbuf;    // tiles: tagged lane words of column cuts (kLeftIn / kRightOut)
+    uint32_t *done;    // tiles: completion flags (the epoch when done)
 };
+
+// One lane waits until a tagged word carries `want`; bounded like every
+// wait (on a timeout the error is raised and the stale value returned).
+static __device__ __noinline__ uint64_t poll_tagged(const uint64_t *p, uint32_t want, int *err, long long limit) {
+    uint64_t v = ld_relaxed_u64(p);
+    if ((uint32_t)(v >> 32) == want) return v;
+    const uint64_t t0 = global_ns();
+    for (;;) {
+        v = ld_relaxed_u64(p);
+        if ((uint32_t)(v >> 32) == want) return v;
+        if (ld_relaxed_i32(err) != 0) return v;
+        if ((long long)(global_ns() - t0) > limit) {
+            raise_error(err, kEtimeout);
+            return v;
+        }
+    }
+}
+
+static __device__ __noinline__ void wait_done(const uint32_t *flag, uint32_t want, int *err, long long limit) {
+    const uint64_t t0 = global_ns();
+    for (;;) {
+        uint32_t v;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(flag) : "memory");
+        if (v == want || ld_relaxed_i32(err) != 0) return;
+        if ((long long)(global_ns() - t0) > limit) {
+            raise_error(err, kEtimeout);
+            return;
+        }
+        __nanosleep(64);
+    }
+}
 
 constexpr int kBatchSrcRing = 8;
 constexpr int kBatchSrcAhead = 4;
@@ -141,6 +187,16 @@ static __device__ __forceinline__ void batch_job(const BatchArgs &P, const SegJo
         }
         if (badsym) atomicCAS(P.err, 0, kEinval);
         uint32_t V = 0xffffffffu;  // zero first column: no vertical steps; bit 31 held at 1
+        if (J.join0 >= 0 || J.join1 >= 0) {  // tiles: the fork-join order
+            if (lane == 0) {
+                if (J.join0 >= 0) wait_done(P.done + J.join0, epoch, P.err, P.wait_limit_ns);
+                if (J.join1 >= 0) wait_done(P.done + J.join1, epoch, P.err, P.wait_limit_ns);
+            }
+            __syncwarp();
+        }
+        if ((J.flags & kLeftIn) && nreal > 0)  // tiles: the left neighbour's last column
+            V = (uint32_t)poll_tagged(P.vbuf + J.vin + lane, epoch, P.err, P.wait_limit_ns) | ~realmask |
+                0x80000000u;
         __syncwarp();
 
         const int64_t nwords = (S + 31) >> 5;
@@ -273,6 +329,13 @@ static __device__ __forceinline__ void batch_job(const BatchArgs &P, const SegJo
 
         if (ok && lane == last && (J.flags & kFinal)) P.len[J.pair] = (int32_t)total;
         if (ok && J.rword >= 0 && nreal > 0) P.rbits[J.rword + lane] = ~V & realmask;
+        if ((J.flags & kRightOut) && nreal > 0)
+            st_relaxed_u64_if(true, P.vbuf + J.vout + lane, ((uint64_t)epoch << 32) | V);
+        if (J.done >= 0) {  // every store of this job before the flag
+            __threadfence();
+            __syncwarp();
+            if (lane == 0) asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(P.done + J.done), "r"(epoch) : "memory");
+        }
 #pragma unroll
         for (int r = 0; r < kLaneRows; ++r) {
             if (r < nreal) {
@@ -482,6 +545,8 @@ void plan_batch(int32_t npairs, const int64_t *a_off, const int64_t *b_off, bool
         int64_t prev_out = -1;
         for (int64_t j = 0; j < nseg; ++j) {
             SegJob J{};
+            J.vin = J.vout = -1;
+            J.join0 = J.join1 = J.done = -1;
             J.rows_off = (tr ? b_off[k] : a_off[k]) + j * seg_rows;
             J.cols_off = cj.dst;
             J.nrows = (int32_t)std::min(seg_rows, L - j * seg_rows);
@@ -547,6 +612,8 @@ void batch_release(paco_ctx *ctx) {
     ctx->batch = nullptr;
     batch_state_free(ctx->recover);
     ctx->recover = nullptr;
+    tile_state_free(ctx->tiles);
+    ctx->tiles = nullptr;
 }
 
 namespace {
@@ -585,6 +652,8 @@ cudaError_t enqueue_batch(paco_ctx *ctx, BatchState *B, const std::array<int, 4>
         A.sigma = sigma;
         A.table_rows = table_rows_for(sigma);
         for (int k = 0; k < kClasses; ++k) A.cls_chunk[k] = cls[(size_t)k];
+        A.vbuf = nullptr;
+        A.done = nullptr;
         const int grid = (int)std::min<int64_t>(B->njobs, (int64_t)ctx->sms * occupancy_for(A.table_rows));
         e = launch_batch(A, grid, st);
         if (e != cudaSuccess) return e;
@@ -810,6 +879,201 @@ int run_batch(paco_ctx *ctx, BatchState *B, const uint8_t *a_cat, const int64_t 
         ctx->last_batch_chunk = C;
     }
     return e == cudaSuccess ? PACO_OK : (e == cudaErrorMemoryAllocation ? PACO_ENOMEM : PACO_EDEVICE);
+}
+
+// ---------------------------------------------------------------------------
+// Tile schedules (PACO partition, PA p x p blocks, PO divide and conquer) on
+// the batch kernel: every tile is one warp job; its top carries and left
+// vertical steps arrive as tagged words written by the tiles above and to
+// the left (a job claims its ticket only after every job it depends on), and
+// the PO fork-join order waits on completion flags.
+// ---------------------------------------------------------------------------
+struct TileLayout {
+    std::vector<SegJob> jobs;
+    int64_t hwords = 0, vwords = 0, nwords = 0, ng = 0;
+    int64_t critical_cells = 0;
+};
+
+struct TileState {
+    DevBuf jobs, coffs, cjob, hbuf, vbuf, rbits, bbits, done, epoch, pjob;
+    std::map<std::tuple<int64_t, int64_t, int, int64_t>, std::shared_ptr<TileLayout>> layouts;
+    int64_t last_tiles = 0, last_critical = 0;
+};
+
+void tile_state_free(TileState *T) {
+    if (!T) return;
+    for (DevBuf *d : {&T->jobs, &T->coffs, &T->cjob, &T->hbuf, &T->vbuf, &T->rbits, &T->bbits, &T->done, &T->epoch,
+                      &T->pjob})
+        if (d->ptr) cudaFree(d->ptr);
+    delete T;
+}
+
+namespace {
+
+__global__ void k_bits_total(const uint32_t *bits, int64_t nw, int32_t *len) {
+    int64_t c = 0;
+    for (int64_t k = threadIdx.x; k < nw; k += blockDim.x) c += __popc(bits[k]);
+    __shared__ int64_t red[32];
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(kFull, c, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        c = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0;
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(kFull, c, o);
+        if (threadIdx.x == 0) *len = (int32_t)c;
+    }
+}
+
+std::shared_ptr<TileLayout> build_tile_layout(int64_t L, int64_t S, int p, int kind, int64_t base) {
+    TilePlan tp;
+    if (!plan_tiles(L, S, p, kind, base, tp)) return nullptr;
+    auto lay = std::make_shared<TileLayout>();
+    std::vector<int64_t> rc, cc;
+    for (const Tile &t : tp.tiles) {
+        rc.push_back(t.r0);
+        rc.push_back(t.r1);
+        cc.push_back(t.c0);
+        cc.push_back(t.c1);
+    }
+    std::sort(rc.begin(), rc.end());
+    rc.erase(std::unique(rc.begin(), rc.end()), rc.end());
+    std::sort(cc.begin(), cc.end());
+    cc.erase(std::unique(cc.begin(), cc.end()), cc.end());
+    auto idx = [](const std::vector<int64_t> &v, int64_t x) {
+        return (int64_t)(std::lower_bound(v.begin(), v.end(), x) - v.begin());
+    };
+    lay->nwords = (S + 31) / 32;
+    const int64_t hstride = (lay->nwords + 1) & ~(int64_t)1;  // even: 16-byte aligned word pairs
+    lay->ng = (L + kLaneRows - 1) / kLaneRows;
+    lay->hwords = (int64_t)rc.size() * hstride;
+    lay->vwords = (int64_t)cc.size() * lay->ng;
+    std::vector<char> is_target(tp.tiles.size(), 0);
+    for (size_t k = 0; k < tp.tiles.size(); ++k) {
+        if (tp.join0[k] >= 0) is_target[(size_t)tp.join0[k]] = 1;
+        if (tp.join1[k] >= 0) is_target[(size_t)tp.join1[k]] = 1;
+    }
+    lay->jobs.reserve(tp.tiles.size());
+    for (size_t k = 0; k < tp.tiles.size(); ++k) {
+        const Tile &t = tp.tiles[k];
+        SegJob J{};
+        J.rows_off = t.r0;
+        J.cols_off = t.c0;
+        J.nrows = (int32_t)(t.r1 - t.r0);
+        J.S = (int32_t)(t.c1 - t.c0);
+        J.pair = 0;
+        J.flags = ((uint32_t)size_class(t.c1 - t.c0) << kClassShift) | (t.r0 > 0 ? kInGlobal : 0u) |
+                  (t.r1 < L ? kOutGlobal : 0u) | (t.c0 > 0 ? kLeftIn : 0u) | (t.c1 < S ? kRightOut : 0u);
+        J.hin = idx(rc, t.r0) * hstride + t.c0 / 32;
+        J.hout = idx(rc, t.r1) * hstride + t.c0 / 32;
+        J.rword = t.c1 == S ? t.r0 / kLaneRows : -1;
+        J.bword = t.r1 == L ? t.c0 / 32 : -1;
+        J.vin = idx(cc, t.c0) * lay->ng + t.r0 / kLaneRows;
+        J.vout = idx(cc, t.c1) * lay->ng + t.r0 / kLaneRows;
+        J.join0 = (int32_t)tp.join0[k];
+        J.join1 = (int32_t)tp.join1[k];
+        J.done = is_target[k] ? (int32_t)k : -1;
+        lay->jobs.push_back(J);
+    }
+    lay->critical_cells = tp.critical_cells;
+    return lay;
+}
+
+}  // namespace
+
+int run_tiles(paco_ctx *ctx, const uint8_t *a, int64_t n, const uint8_t *b, int64_t m, int32_t *bottom_row,
+              int32_t *right_col, int32_t *len, cudaStream_t st) {
+    const bool tr = m > n;
+    const int64_t L = tr ? m : n, S = tr ? n : m;
+    const uint8_t *ka = tr ? b : a, *kb = tr ? a : b;
+    const int kind = ctx->opt_tiles;
+    const int64_t base = ctx->opt_tile_base > 0 ? ctx->opt_tile_base : (kind == kTilesPo ? 16 : 4);
+    if (!ctx->tiles) ctx->tiles = new (std::nothrow) TileState();
+    TileState *T = ctx->tiles;
+    if (!T) return PACO_ENOMEM;
+    const auto key = std::make_tuple(L, S, kind, base);
+    auto it = T->layouts.find(key);
+    std::shared_ptr<TileLayout> lay;
+    if (it != T->layouts.end()) {
+        lay = it->second;
+    } else {
+        lay = build_tile_layout(L, S, ctx->sms, kind, base);
+        if (!lay) return PACO_EINVAL;
+        if (T->layouts.size() > 16) T->layouts.clear();
+        T->layouts.emplace(key, lay);
+    }
+    const int64_t njobs = (int64_t)lay->jobs.size();
+    int rc;
+    if ((rc = ensure_bytes(ctx, T->jobs, (size_t)njobs * sizeof(SegJob) + 64)) != PACO_OK) return rc;
+    if ((rc = ensure_bytes(ctx, T->coffs, (size_t)S * 4 + 64)) != PACO_OK) return rc;
+    if ((rc = ensure_bytes(ctx, T->cjob, sizeof(ColJob) + 64)) != PACO_OK) return rc;
+    if ((rc = ensure_bytes(ctx, T->hbuf, (size_t)lay->hwords * 8 + 64)) != PACO_OK) return rc;
+    if ((rc = ensure_bytes(ctx, T->vbuf, (size_t)lay->vwords * 8 + 64)) != PACO_OK) return rc;
+    if ((rc = ensure_bytes(ctx, T->rbits, (size_t)lay->ng * 4 + 64)) != PACO_OK) return rc;
+    if ((rc = ensure_bytes(ctx, T->bbits, (size_t)lay->nwords * 4 + 64)) != PACO_OK) return rc;
+    if ((rc = ensure_bytes(ctx, T->done, (size_t)njobs * 4 + 64)) != PACO_OK) return rc;
+    if ((rc = ensure_bytes(ctx, T->epoch, 64)) != PACO_OK) return rc;
+    if ((rc = ensure_bytes(ctx, T->pjob, sizeof(PrefixJob) + 64)) != PACO_OK) return rc;
+    ColJob cj{};
+    cj.src = 0;
+    cj.dst = 0;
+    cj.len = S;
+    cj.from_a = 0;  // the streamed string is passed as b_cat
+    PrefixJob pj{};
+    pj.bword = 0;
+    pj.rword = 0;
+    pj.L = L;
+    pj.S = S;
+    pj.out_bottom = 0;
+    pj.out_right = 0;
+    pj.transposed = tr ? 1 : 0;
+    cudaError_t e = cudaMemcpyAsync(T->jobs.ptr, lay->jobs.data(), (size_t)njobs * sizeof(SegJob),
+                                    cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(T->cjob.ptr, &cj, sizeof(cj), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(T->pjob.ptr, &pj, sizeof(pj), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ticket_ptr(), 0, sizeof(int), st);
+    if (e != cudaSuccess) return set_cuda_error(ctx, e, "tile layout");
+    k_bump_epoch<<<1, 1, 0, st>>>((uint32_t *)T->epoch.ptr);
+    k_pair_column_offsets<<<1, 256, 0, st>>>(kb, kb, (const ColJob *)T->cjob.ptr, (uint32_t *)T->coffs.ptr,
+                                             kMaxSigma, ctx->err_ptr());
+    BatchArgs A;
+    A.a_cat = ka;
+    A.b_cat = kb;
+    A.coffs = (const uint32_t *)T->coffs.ptr;
+    A.jobs = (const SegJob *)T->jobs.ptr;
+    A.njobs = njobs;
+    A.hbuf = (uint64_t *)T->hbuf.ptr;
+    A.rbits = (uint32_t *)T->rbits.ptr;
+    A.bbits = (uint32_t *)T->bbits.ptr;
+    A.len = len;
+    A.ticket = ctx->ticket_ptr();
+    A.err = ctx->err_ptr();
+    A.epoch_dev = (const uint32_t *)T->epoch.ptr;
+    A.wait_limit_ns = ctx->wait_limit_ns;
+    A.sigma = kMaxSigma;
+    A.table_rows = table_rows_for(kMaxSigma);
+    const int force = ctx->opt_chunk;
+    const int cls_default[4] = {2, 4, 8, 8};
+    for (int k = 0; k < kClasses; ++k) A.cls_chunk[k] = force ? force : cls_default[k];
+    A.vbuf = (uint64_t *)T->vbuf.ptr;
+    A.done = (uint32_t *)T->done.ptr;
+    const int grid = (int)std::min<int64_t>(njobs, (int64_t)ctx->sms * occupancy_for(A.table_rows));
+    cudaEventRecord(ctx->ev0, st);
+    e = launch_batch(A, grid, st);
+    cudaEventRecord(ctx->ev1, st);
+    ctx->timed = true;
+    ctx->timed_name = "k_batch (tile schedule)";
+    if (e != cudaSuccess) return set_cuda_error(ctx, e, "tile schedule launch");
+    if (bottom_row || right_col) {
+        k_batch_prefix<<<1, 256, 0, st>>>((const PrefixJob *)T->pjob.ptr, (const uint32_t *)T->bbits.ptr,
+                                          (const uint32_t *)T->rbits.ptr, bottom_row, right_col);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return set_cuda_error(ctx, e, "tile schedule boundaries");
+    }
+    if (len) k_bits_total<<<1, 256, 0, st>>>((const uint32_t *)T->bbits.ptr, lay->nwords, len);
+    T->last_tiles = njobs;
+    T->last_critical = lay->critical_cells;
+    e = cudaGetLastError();
+    return e == cudaSuccess ? PACO_OK : set_cuda_error(ctx, e, "tile schedule length");
 }
 
 }  // namespace paco

@@ -19,6 +19,7 @@ struct DevBuf {
 namespace paco {
 struct BatchState;
 struct ServeEngine;
+struct TileState;
 
 // A pair plan plus its strip offsets resident on the device.
 struct CachedPairPlan {
@@ -40,6 +41,8 @@ struct paco_ctx {
     DevBuf h_a, h_b, h_top, h_left, h_row, h_col, h_len;
     uint32_t epoch = 0;
     int opt_engine = 0, opt_chunk = 0, opt_warps = 0, opt_orient = 0, opt_schedule = 0, opt_wpl = 0;
+    int opt_tiles = 0;            // single pair: 0 = strip pipeline, 1..3 = tile schedule (PACO, PA, PO)
+    int64_t opt_tile_base = 0;    // tile schedules: smallest tile side in granules (0 = per schedule)
     int test_stall = -1;
     int opt_alphabet = 256;
     long long wait_limit_ns = 2000000000LL;
@@ -52,6 +55,7 @@ struct paco_ctx {
     std::map<std::tuple<int64_t, int64_t, int, int, int, int>, std::unique_ptr<paco::CachedPairPlan>> plans;
     paco::BatchState *batch = nullptr;
     paco::BatchState *recover = nullptr;  // the subsequence recovery's batch engine state
+    paco::TileState *tiles = nullptr;     // tile schedules: layouts and buffers
     paco::ServeEngine *serve = nullptr;
 
     int *err_ptr() { return (int *)small.ptr; }
@@ -76,5 +80,9 @@ int run_batch(paco_ctx *ctx, BatchState *B, const uint8_t *a_cat, const int64_t 
               const int64_t *h_row_off, int32_t *cols_cat, const int64_t *h_col_off, cudaStream_t st,
               bool use_graph, int force_chunk, int sigma);
 void serve_shutdown(paco_ctx *ctx);
+// A tile schedule (ctx->opt_tiles) of one pair with zero boundaries.
+int run_tiles(paco_ctx *ctx, const uint8_t *a, int64_t n, const uint8_t *b, int64_t m, int32_t *bottom_row,
+              int32_t *right_col, int32_t *len, cudaStream_t st);
+void tile_state_free(TileState *T);
 void batch_release(paco_ctx *ctx);
 }  // namespace paco

@@ -73,6 +73,13 @@ int run_pair(paco_ctx *ctx, const uint8_t *a, int64_t n, const uint8_t *b, int64
         ctx->timed = false;
         return set_cuda_error(ctx, e, "degenerate table");
     }
+    if (ctx->opt_tiles) {  // a tile schedule instead of the strip pipeline
+        if (top || left) {
+            std::snprintf(ctx->last_error, sizeof(ctx->last_error), "tile schedules take zero boundaries only");
+            return PACO_EINVAL;
+        }
+        return run_tiles(ctx, a, n, b, m, bottom_row, right_col, len, st);
+    }
     int rc = PACO_OK;
     const CachedPairPlan *cp = get_pair_plan(ctx, n, m, &rc);
     if (!cp) return rc;

@@ -2,6 +2,7 @@
 #include "plan.hpp"
 
 #include <algorithm>
+#include <utility>
 #include <cmath>
 #include <map>
 #include <queue>
@@ -225,6 +226,124 @@ bool plan_pair(int64_t n, int64_t m, int sms, const PairPlanOptions &o, PairPlan
     }
     out.nstrips = (int)nstrips;
     out.grid = o.resident > 0 ? (int)std::min<int64_t>(nstrips, o.resident) : (int)nstrips;
+    return true;
+}
+
+namespace {
+
+struct GTile {  // a tile in granules
+    int64_t r0, r1, c0, c1;
+};
+
+// PO recursion: base tiles in fork-join order; returns (first, last) tile
+// index of the node, and adds the join dependencies.
+std::pair<int64_t, int64_t> po_node(int64_t r0, int64_t r1, int64_t c0, int64_t c1, int64_t base,
+                                    std::vector<GTile> &out, std::vector<std::vector<int64_t>> &joins) {
+    const bool split_r = (r1 - r0) > base, split_c = (c1 - c0) > base;
+    if (!split_r && !split_c) {
+        out.push_back({r0, r1, c0, c1});
+        joins.emplace_back();
+        const int64_t k = (int64_t)out.size() - 1;
+        return {k, k};
+    }
+    const int64_t rm = split_r ? r0 + (r1 - r0) / 2 : r1, cm = split_c ? c0 + (c1 - c0) / 2 : c1;
+    auto dep = [&](int64_t first, int64_t on) { joins[(size_t)first].push_back(on); };
+    if (split_r && split_c) {
+        auto x11 = po_node(r0, rm, c0, cm, base, out, joins);
+        auto x12 = po_node(r0, rm, cm, c1, base, out, joins);
+        dep(x12.first, x11.second);
+        auto x21 = po_node(rm, r1, c0, cm, base, out, joins);
+        dep(x21.first, x11.second);
+        auto x22 = po_node(rm, r1, cm, c1, base, out, joins);
+        dep(x22.first, x12.second);
+        dep(x22.first, x21.second);
+        return {x11.first, x22.second};
+    }
+    auto h1 = split_r ? po_node(r0, rm, c0, c1, base, out, joins) : po_node(r0, r1, c0, cm, base, out, joins);
+    auto h2 = split_r ? po_node(rm, r1, c0, c1, base, out, joins) : po_node(r0, r1, cm, c1, base, out, joins);
+    dep(h2.first, h1.second);
+    return {h1.first, h2.second};
+}
+
+}  // namespace
+
+bool plan_tiles(int64_t n, int64_t m, int p, int kind, int64_t base, TilePlan &out) {
+    out = TilePlan();
+    if (n <= 0 || m <= 0 || p <= 0 || base <= 0) return false;
+    const int64_t ng = (n + kTileRowGranule - 1) / kTileRowGranule;
+    const int64_t mg = (m + kTileColGranule - 1) / kTileColGranule;
+    std::vector<GTile> g;
+    std::vector<std::vector<int64_t>> joins;  // extra dependencies (PO), by granule tile
+    if (kind == kTilesPaco) {
+        std::vector<Tile> t;
+        if (!paco_partition(ng, mg, p, base, t)) return false;
+        for (const Tile &x : t) g.push_back({x.r0, x.r1, x.c0, x.c1});
+    } else if (kind == kTilesPa) {
+        const std::vector<int64_t> hs = balanced_split(ng, std::min<int64_t>(p, ng));
+        const std::vector<int64_t> ws = balanced_split(mg, std::min<int64_t>(p, mg));
+        std::vector<int64_t> r(hs.size() + 1, 0), c(ws.size() + 1, 0);
+        for (size_t i = 0; i < hs.size(); ++i) r[i + 1] = r[i] + hs[i];
+        for (size_t j = 0; j < ws.size(); ++j) c[j + 1] = c[j] + ws[j];
+        const int64_t P = (int64_t)hs.size(), Q = (int64_t)ws.size();
+        for (int64_t d = 0; d <= P + Q - 2; ++d)
+            for (int64_t i = std::max<int64_t>(0, d - Q + 1); i <= std::min<int64_t>(d, P - 1); ++i)
+                g.push_back({r[(size_t)i], r[(size_t)i + 1], c[(size_t)(d - i)], c[(size_t)(d - i) + 1]});
+    } else if (kind == kTilesPo) {
+        po_node(0, ng, 0, mg, base, g, joins);
+    } else {
+        return false;
+    }
+    if (joins.empty()) joins.resize(g.size());
+    // bands of at most one warp's rows, in order; a join dependency moves to
+    // the first band of its tile and points at the last band of the other
+    std::vector<int64_t> first_band(g.size()), last_band(g.size());
+    std::vector<Tile> tiles;
+    for (size_t k = 0; k < g.size(); ++k) {
+        first_band[k] = (int64_t)tiles.size();
+        for (int64_t r = g[k].r0; r < g[k].r1; r += kTileMaxRowGranules) {
+            const int64_t re = std::min(g[k].r1, r + kTileMaxRowGranules);
+            Tile t{};
+            t.r0 = std::min(n, r * kTileRowGranule);
+            t.r1 = std::min(n, re * kTileRowGranule);
+            t.c0 = std::min(m, g[k].c0 * kTileColGranule);
+            t.c1 = std::min(m, g[k].c1 * kTileColGranule);
+            t.order = (int64_t)tiles.size();
+            tiles.push_back(t);
+        }
+        last_band[k] = (int64_t)tiles.size() - 1;
+    }
+    std::vector<std::vector<int64_t>> deps;
+    tile_deps(tiles, deps);
+    out.join0.assign(tiles.size(), -1);
+    out.join1.assign(tiles.size(), -1);
+    for (size_t k = 0; k < g.size(); ++k) {
+        const size_t fb = (size_t)first_band[k];
+        for (int64_t on : joins[k]) {
+            const int64_t target = last_band[(size_t)on];
+            deps[fb].push_back(target);
+            if (out.join0[fb] < 0) out.join0[fb] = target;
+            else if (out.join1[fb] < 0 && out.join0[fb] != target) out.join1[fb] = target;
+            else if (out.join0[fb] != target && out.join1[fb] != target) return false;  // at most two
+        }
+    }
+    out.dep_off.assign(tiles.size() + 1, 0);
+    std::vector<int64_t> finish(tiles.size(), 0);
+    for (size_t k = 0; k < tiles.size(); ++k) {
+        std::vector<int64_t> &d = deps[k];
+        std::sort(d.begin(), d.end());
+        d.erase(std::unique(d.begin(), d.end()), d.end());
+        int64_t start = 0;
+        for (int64_t x : d) {
+            if (x >= (int64_t)k) return false;  // not a topological order
+            out.dep_idx.push_back(x);
+            start = std::max(start, finish[(size_t)x]);
+        }
+        out.dep_off[k + 1] = (int64_t)out.dep_idx.size();
+        const Tile &t = tiles[k];
+        finish[k] = start + (t.r1 - t.r0) * (t.c1 - t.c0);
+        out.critical_cells = std::max(out.critical_cells, finish[k]);
+    }
+    out.tiles.swap(tiles);
     return true;
 }
 

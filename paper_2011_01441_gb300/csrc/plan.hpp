@@ -69,4 +69,32 @@ bool plan_pair(int64_t n, int64_t m, int sms, const PairPlanOptions &o, PairPlan
 // Balanced integer split of `total` units into `parts` (first total%parts get one more).
 std::vector<int64_t> balanced_split(int64_t total, int64_t parts);
 
+// ---- tile schedules: the paper's comparison (PACO against PA and PO) ----
+//
+// All three cut the table into tiles on a grid of 31-row x 64-column
+// granules (a lane's rows, two carry words' columns) and run them as a
+// dataflow: a tile starts when the tiles it depends on are done.
+//   kTilesPaco: the PACO partition above, computed on the granule grid.
+//   kTilesPa:   the processor-aware p-way division of Chowdhury and
+//               Ramachandran: a p x p grid of blocks in anti-diagonal order,
+//               critical path (2p - 1) blocks of n m / p^2 cells.
+//   kTilesPo:   the processor-oblivious 2-way divide and conquer: X11, then
+//               X12 and X21, then X22, recursively down to base tiles, with
+//               the fork-join order as extra dependencies (a quadrant starts
+//               only when the quadrants before it are complete).
+// Tiles taller than one warp (32 granules = 992 rows) are cut into bands.
+enum TileKind { kTilesPaco = 1, kTilesPa = 2, kTilesPo = 3 };
+struct TilePlan {
+    std::vector<Tile> tiles;           // execution order; rows/columns in cells
+    std::vector<int64_t> dep_off;      // tiles.size()+1 offsets into dep_idx
+    std::vector<int64_t> dep_idx;      // each dependency precedes its tile
+    std::vector<int64_t> join0, join1; // per tile: fork-join dependencies (PO), -1 if none
+    int64_t critical_cells = 0;        // heaviest dependency path, in cells
+};
+constexpr int64_t kTileRowGranule = 31;
+constexpr int64_t kTileColGranule = 64;
+constexpr int64_t kTileMaxRowGranules = 32;  // one warp's rows
+// base: the smallest tile side in granules (PACO stop, PO base).
+bool plan_tiles(int64_t n, int64_t m, int p, int kind, int64_t base, TilePlan &out);
+
 }  // namespace paco

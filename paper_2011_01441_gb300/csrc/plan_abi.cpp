@@ -71,4 +71,30 @@ int paco_plan_pair(int64_t n, int64_t m, int32_t sms, int32_t chunk, int32_t war
     return 0;
 }
 
+int paco_plan_tiles(int64_t n, int64_t m, int32_t p, int32_t kind, int64_t base, paco_tile *out,
+                    int64_t cap, int64_t *count, int64_t *dep_off, int64_t *dep_idx, int64_t cap_idx,
+                    int64_t *n_idx, int64_t *critical_cells) {
+    paco::TilePlan tp;
+    if (!paco::plan_tiles(n, m, p, kind, base, tp)) return -1;
+    const int64_t T = (int64_t)tp.tiles.size();
+    if (count) *count = T;
+    if (n_idx) *n_idx = (int64_t)tp.dep_idx.size();
+    if (critical_cells) *critical_cells = tp.critical_cells;
+    for (int64_t k = 0; out && k < T && k < cap; ++k) {
+        const paco::Tile &t = tp.tiles[(size_t)k];
+        out[k].r0 = t.r0;
+        out[k].r1 = t.r1;
+        out[k].c0 = t.c0;
+        out[k].c1 = t.c1;
+        out[k].label = 0;
+        out[k].owner = 0;
+        out[k].order = k;
+    }
+    if (dep_off && cap >= T)
+        for (int64_t k = 0; k <= T; ++k) dep_off[k] = tp.dep_off[(size_t)k];
+    for (int64_t k = 0; dep_idx && k < (int64_t)tp.dep_idx.size() && k < cap_idx; ++k)
+        dep_idx[k] = tp.dep_idx[(size_t)k];
+    return 0;
+}
+
 }  // extern "C"

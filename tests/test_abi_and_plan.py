@@ -179,3 +179,42 @@ def test_pair_plan_options(lib):
     pl = P.paco_plan_pair(5000, 7000, 152, chunk=4, warps=2, orient=1, schedule=1)
     assert pl["transpose"] == 0 and pl["chunk"] == 4 and pl["warps"] == 2
     assert list(pl["row0"]) == [0, 1984, 3968, 5000]
+
+
+@pytest.mark.parametrize("kind", [1, 2, 3])
+@pytest.mark.parametrize("n,m,p,base", [(131072, 131072, 152, 4), (5000, 3001, 7, 2), (62, 64, 4, 1),
+                                        (100000, 1000, 152, 4)])
+def test_tile_schedules_cover_and_order(lib, kind, n, m, p, base):
+    """Tiles cover the table exactly, are at most 992 rows, sit on the
+    31 x 64 granule grid, and every dependency precedes its tile."""
+    t = P.paco_plan_tiles(n, m, p, kind, base)
+    cells = 0
+    for k, x in enumerate(t["tiles"]):
+        assert 0 <= x["r0"] < x["r1"] <= n and 0 <= x["c0"] < x["c1"] <= m
+        assert x["r1"] - x["r0"] <= 992
+        assert x["r0"] % 31 == 0 and (x["r1"] % 31 == 0 or x["r1"] == n)
+        assert x["c0"] % 64 == 0 and (x["c1"] % 64 == 0 or x["c1"] == m)
+        cells += (x["r1"] - x["r0"]) * (x["c1"] - x["c0"])
+        deps = t["dep_idx"][t["dep_off"][k]:t["dep_off"][k + 1]]
+        assert np.all(deps < k)
+    assert cells == n * m
+    if n * m < 1e7:  # exact cover, cell by cell
+        cover = np.zeros((n, m), dtype=np.int8)
+        for x in t["tiles"]:
+            cover[x["r0"]:x["r1"], x["c0"]:x["c1"]] += 1
+        assert np.all(cover == 1)
+    assert t["critical_cells"] > 0
+
+
+def test_tile_schedule_critical_paths_follow_the_paper():
+    """On a 131072-square table with p = 152: PA's critical path is 2 n m / p
+    (its (2p - 1) blocks), PACO's is shorter, PO's fork-join path longer."""
+    n = m = 131072
+    p = 152
+    unit = n * m / p
+    pa = P.paco_plan_tiles(n, m, p, 2, 4)["critical_cells"] / unit
+    paco = P.paco_plan_tiles(n, m, p, 1, 4)["critical_cells"] / unit
+    po = P.paco_plan_tiles(n, m, p, 3, 16)["critical_cells"] / unit
+    assert 1.95 < pa < 2.05
+    assert paco < pa
+    assert po > pa
