@@ -156,7 +156,7 @@ constexpr int kColAhead = 8;
 // One warp job (a segment of up to 32 lanes x 31 rows of one pair, all its
 // columns) with chunk width C.  The pipeline ends at the segment's last
 // real lane: that lane hands the bottom row on.
-template <int C>
+template <int C, bool TILES>
 static __device__ __forceinline__ void batch_job(const BatchArgs &P, const SegJob &J, const int lane, uint32_t *pm,
                                                  const uint32_t pm_lane, uint32_t *cols_ptr, const uint32_t col_ring,
                                                  const uint32_t src_ring, const uint32_t epoch) {
@@ -187,14 +187,14 @@ static __device__ __forceinline__ void batch_job(const BatchArgs &P, const SegJo
         }
         if (badsym) atomicCAS(P.err, 0, kEinval);
         uint32_t V = 0xffffffffu;  // zero first column: no vertical steps; bit 31 held at 1
-        if (J.join0 >= 0 || J.join1 >= 0) {  // tiles: the fork-join order
+        if (TILES && (J.join0 >= 0 || J.join1 >= 0)) {  // tiles: the fork-join order
             if (lane == 0) {
                 if (J.join0 >= 0) wait_done(P.done + J.join0, epoch, P.err, P.wait_limit_ns);
                 if (J.join1 >= 0) wait_done(P.done + J.join1, epoch, P.err, P.wait_limit_ns);
             }
             __syncwarp();
         }
-        if ((J.flags & kLeftIn) && nreal > 0)  // tiles: the left neighbour's last column
+        if (TILES && (J.flags & kLeftIn) && nreal > 0)  // tiles: the left neighbour's last column
             V = (uint32_t)poll_tagged(P.vbuf + J.vin + lane, epoch, P.err, P.wait_limit_ns) | ~realmask |
                 0x80000000u;
         __syncwarp();
@@ -329,9 +329,9 @@ static __device__ __forceinline__ void batch_job(const BatchArgs &P, const SegJo
 
         if (ok && lane == last && (J.flags & kFinal)) P.len[J.pair] = (int32_t)total;
         if (ok && J.rword >= 0 && nreal > 0) P.rbits[J.rword + lane] = ~V & realmask;
-        if ((J.flags & kRightOut) && nreal > 0)
+        if (TILES && (J.flags & kRightOut) && nreal > 0)
             st_relaxed_u64_if(true, P.vbuf + J.vout + lane, ((uint64_t)epoch << 32) | V);
-        if (J.done >= 0) {  // every store of this job before the flag
+        if (TILES && J.done >= 0) {  // every store of this job before the flag
             __threadfence();
             __syncwarp();
             if (lane == 0) asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(P.done + J.done), "r"(epoch) : "memory");
@@ -347,6 +347,9 @@ static __device__ __forceinline__ void batch_job(const BatchArgs &P, const SegJo
     }
 }
 
+// TILES: the jobs are tiles of one table (tagged left/right columns, join
+// flags); a separate instantiation keeps plain batches at fewer registers.
+template <bool TILES>
 __global__ void __launch_bounds__(32) k_batch(const BatchArgs P) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ __align__(16) uint64_t s_src[2 * kBatchSrcRing];
@@ -371,9 +374,9 @@ __global__ void __launch_bounds__(32) k_batch(const BatchArgs P) {
         // the chunk width of the job's size class
         const int cl = (int)((J.flags >> kClassShift) & 3u);  // (no dynamic index into the parameters)
         const int C = cl == 0 ? P.cls_chunk[0] : (cl == 1 ? P.cls_chunk[1] : (cl == 2 ? P.cls_chunk[2] : P.cls_chunk[3]));
-        if (C == 2) batch_job<2>(P, J, lane, pm, pm_lane, s_cols, col_ring, src_ring, epoch);
-        else if (C == 4) batch_job<4>(P, J, lane, pm, pm_lane, s_cols, col_ring, src_ring, epoch);
-        else batch_job<8>(P, J, lane, pm, pm_lane, s_cols, col_ring, src_ring, epoch);
+        if (C == 2) batch_job<2, TILES>(P, J, lane, pm, pm_lane, s_cols, col_ring, src_ring, epoch);
+        else if (C == 4) batch_job<4, TILES>(P, J, lane, pm, pm_lane, s_cols, col_ring, src_ring, epoch);
+        else batch_job<8, TILES>(P, J, lane, pm, pm_lane, s_cols, col_ring, src_ring, epoch);
     }
 }
 
@@ -462,23 +465,33 @@ __global__ void k_batch_prefix(const PrefixJob *pj, const uint32_t *bbits, const
     else if (kr) for (int64_t i = threadIdx.x; i <= J.L; i += blockDim.x) kr[i] = 0;
 }
 
-cudaError_t launch_batch(const BatchArgs &a, int grid, cudaStream_t st) {
+template <bool TILES>
+cudaError_t launch_batch_t(const BatchArgs &a, int grid, cudaStream_t st) {
     const size_t smem = (size_t)a.table_rows * 32 * 4;
-    cudaError_t e = cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_batch<TILES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)((kMaxSigma + 1) * 32 * 4));
     if (e != cudaSuccess) return e;
-    k_batch<<<grid, 32, smem, st>>>(a);
+    k_batch<TILES><<<grid, 32, smem, st>>>(a);
     return cudaGetLastError();
 }
 
-int occupancy_for(int table_rows) {
+cudaError_t launch_batch(const BatchArgs &a, int grid, cudaStream_t st) {
+    return a.vbuf ? launch_batch_t<true>(a, grid, st) : launch_batch_t<false>(a, grid, st);
+}
+
+template <bool TILES>
+int occupancy_t(int table_rows) {
     const size_t smem = (size_t)table_rows * 32 * 4;
-    if (cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)((kMaxSigma + 1) * 32 * 4)) !=
-        cudaSuccess)
+    if (cudaFuncSetAttribute(k_batch<TILES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)((kMaxSigma + 1) * 32 * 4)) != cudaSuccess)
         return 1;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch, 32, smem) != cudaSuccess) return 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_batch<TILES>, 32, smem) != cudaSuccess) return 1;
     return std::max(1, nb);
+}
+
+int occupancy_for(int table_rows, bool tiles = false) {
+    return tiles ? occupancy_t<true>(table_rows) : occupancy_t<false>(table_rows);
 }
 
 int table_rows_for(int sigma) { return (sigma >= kMaxSigma ? kMaxSigma : sigma) + 1; }
@@ -1056,7 +1069,7 @@ int run_tiles(paco_ctx *ctx, const uint8_t *a, int64_t n, const uint8_t *b, int6
     for (int k = 0; k < kClasses; ++k) A.cls_chunk[k] = force ? force : cls_default[k];
     A.vbuf = (uint64_t *)T->vbuf.ptr;
     A.done = (uint32_t *)T->done.ptr;
-    const int grid = (int)std::min<int64_t>(njobs, (int64_t)ctx->sms * occupancy_for(A.table_rows));
+    const int grid = (int)std::min<int64_t>(njobs, (int64_t)ctx->sms * occupancy_for(A.table_rows, true));
     cudaEventRecord(ctx->ev0, st);
     e = launch_batch(A, grid, st);
     cudaEventRecord(ctx->ev1, st);
