@@ -14,10 +14,19 @@ caller-given first row/column, see `lcs_oracle.c`):
   (the bit-vector LCS of Allison & Dix / Hyyro, `lcs_bitpar.c`), zero
   boundaries only: a cross-check of the DP on large inputs, not the
   definition
+* `affine(a, b, match, mismatch, gap_open, gap_extend)` -> (score,
+  bottom_row[m+1], right_col[n+1]): global alignment with affine gap costs,
+  the variant the footnote to Eq. (1) names (Gotoh's recurrence,
+  `affine_oracle.c`)
+* `affine_batch(a_cat, a_off, b_cat, b_off, scores, threads)` -> per-pair
+  scores
 
 Pins that tie it to something other than itself live in
 `tests/test_oracle_pins.py` (brute-force enumeration, indel distance,
-closed forms, invariants, the CLRS worked example).
+closed forms, invariants, the CLRS worked example) and
+`tests/test_oracle_affine_pins.py` (enumeration of every alignment, the
+LCS, Levenshtein and indel special cases, gap-block closed forms,
+symmetries).
 """
 from __future__ import annotations
 
@@ -31,6 +40,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lcs_oracle.c")
 _SRC_BITPAR = os.path.join(_HERE, "lcs_bitpar.c")
+_SRC_AFFINE = os.path.join(_HERE, "affine_oracle.c")
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -38,11 +48,11 @@ _lib = None
 
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (plain C, -O2, no vector intrinsics)."""
-    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_BITPAR))
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_BITPAR), os.path.getmtime(_SRC_AFFINE))
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < newest:
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-pthread",
-                               _SRC, _SRC_BITPAR, "-o", tmp])
+                               _SRC, _SRC_BITPAR, _SRC_AFFINE, "-o", tmp])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -63,6 +73,10 @@ def _load():
             lib.oracle_lcs_batch.restype = ctypes.c_int
             lib.oracle_lcs_bitpar.argtypes = [P, I64, P, I64, P, P, P]
             lib.oracle_lcs_bitpar.restype = ctypes.c_int
+            lib.oracle_affine.argtypes = [P, I64, P, I64, I64, I64, I64, I64, P, P, P]
+            lib.oracle_affine.restype = ctypes.c_int
+            lib.oracle_affine_batch.argtypes = [P, P, P, P, I64, I64, I64, I64, I64, P, ctypes.c_int]
+            lib.oracle_affine_batch.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -158,3 +172,39 @@ def lcs_bitpar(a, b):
     if rc != 0:
         raise RuntimeError(f"oracle_lcs_bitpar failed ({rc})")
     return int(L.value), row, col
+
+
+def affine(a, b, match, mismatch, gap_open, gap_extend):
+    """(score, bottom_row[m+1], right_col[n+1]) of global alignment with
+    affine gap costs: +match / -mismatch per aligned column, a gap run of k
+    columns costs gap_open + k * gap_extend (all four >= 0)."""
+    a = _u8(a)
+    b = _u8(b)
+    n, m = a.size, b.size
+    score = ctypes.c_int64(0)
+    row = np.empty(m + 1, dtype=np.int64)
+    col = np.empty(n + 1, dtype=np.int64)
+    rc = _load().oracle_affine(_ptr(a) if n else None, n, _ptr(b) if m else None, m, int(match), int(mismatch),
+                               int(gap_open), int(gap_extend), ctypes.byref(score), _ptr(row), _ptr(col))
+    if rc != 0:
+        raise ValueError(f"oracle_affine failed ({rc})")
+    return int(score.value), row, col
+
+
+def affine_batch(a_cat, a_off, b_cat, b_off, scores, threads=None):
+    """Per-pair scores (int64[npairs]); `scores` = (match, mismatch,
+    gap_open, gap_extend); pairs spread over `threads` host threads."""
+    a_cat = _u8(a_cat)
+    b_cat = _u8(b_cat)
+    a_off = np.ascontiguousarray(a_off, dtype=np.int64)
+    b_off = np.ascontiguousarray(b_off, dtype=np.int64)
+    npairs = a_off.size - 1
+    out = np.zeros(npairs, dtype=np.int64)
+    if threads is None:
+        threads = os.cpu_count() or 1
+    M, X, O, E = (int(v) for v in scores)
+    rc = _load().oracle_affine_batch(_ptr(a_cat), _ptr(a_off), _ptr(b_cat), _ptr(b_off), npairs, M, X, O, E,
+                                     _ptr(out), int(threads))
+    if rc != 0:
+        raise ValueError(f"oracle_affine_batch failed ({rc})")
+    return out
