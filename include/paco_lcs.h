@@ -115,6 +115,8 @@ enum paco_option {
                                    kernel, for the paper's comparison; zero boundaries only */
     PACO_OPT_TILE_BASE = 11,    /* tile schedules: smallest tile side in 31-row / 64-column
                                    granules (0 = 4 for PACO, 16 for PO) */
+    PACO_OPT_AFFINE_ROWS = 12,  /* affine alignment (include/paco_affine.h): rows per
+                                   lane of a row band, 2, 4 or 8 (0 = 4) */
     PACO_OPT_TEST_STALL = 100   /* tests only: make one strip wait on a flag
                                    nothing sets (exercises the bounded wait) */
 };

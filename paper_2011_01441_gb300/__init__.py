@@ -1,4 +1,5 @@
-"""Python binding of the GB300 LCS library (include/paco_lcs.h, include/paco_plan.h).
+"""Python binding of the GB300 LCS library (include/paco_lcs.h, include/paco_plan.h,
+include/paco_affine.h).
 
 Argument marshalling only: every step of the computation runs in the CUDA
 kernels of libpaco_lcs.so.  Device buffers are torch CUDA tensors (torch is
@@ -38,6 +39,7 @@ OPT_BATCH_CHUNKS = 8
 OPT_WORDS_PER_LANE = 9
 OPT_TILES = 10
 OPT_TILE_BASE = 11
+OPT_AFFINE_ROWS = 12
 OPT_TEST_STALL = 100
 
 _lib = None
@@ -59,6 +61,11 @@ class PacoPairPlan(ctypes.Structure):
     _fields_ = [("transpose", ctypes.c_int32), ("chunk", ctypes.c_int32), ("warps", ctypes.c_int32),
                 ("nstrips", ctypes.c_int32), ("words_per_lane", ctypes.c_int32), ("pad", ctypes.c_int32),
                 ("L", ctypes.c_int64), ("S", ctypes.c_int64)]
+
+
+class PacoAffineScores(ctypes.Structure):
+    _fields_ = [("match", ctypes.c_int32), ("mismatch", ctypes.c_int32), ("gap_open", ctypes.c_int32),
+                ("gap_extend", ctypes.c_int32)]
 
 
 class PacoServeStats(ctypes.Structure):
@@ -101,6 +108,9 @@ def load():
         "paco_plan_partition_deps": ([I64, I64, I32, I64, P, P, I64, ctypes.POINTER(I64)], INT),
         "paco_plan_pair": ([I64, I64, I32, I32, I32, I32, I32, I32, ctypes.POINTER(PacoPairPlan), P, I64], INT),
         "paco_plan_tiles": ([I64, I64, I32, I32, I64, P, I64, P, P, P, I64, P, P], INT),
+        "paco_affine_align": ([P, P, I64, P, I64, ctypes.POINTER(PacoAffineScores), P, P, P, P], INT),
+        "paco_affine_align_host": ([P, P, I64, P, I64, ctypes.POINTER(PacoAffineScores), P, P, P, P], INT),
+        "paco_affine_batch": ([P, P, P, P, P, I32, ctypes.POINTER(PacoAffineScores), P, P], INT),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -281,6 +291,52 @@ def paco_lcs_batch(ctx: Context, a_cat, b_cat, h_a_off, h_b_off, lengths=None, r
                                  _ptr(lengths), _ptr(rows_cat), p(ro), _ptr(cols_cat), p(co),
                                  _stream(stream)), ctx)
     return lengths
+
+
+def _scores(scores):
+    M, X, O, E = (int(v) for v in scores)
+    return ctypes.byref(PacoAffineScores(M, X, O, E))
+
+
+def paco_affine_align(ctx: Context, a, b, scores, score=None, bottom_row=None, right_col=None,
+                      want_rows=False, want_cols=False, stream=None):
+    """Global alignment with affine gap costs of device strings a (rows) and
+    b (columns); scores = (match, mismatch, gap_open, gap_extend).  Returns
+    (score int32[1], bottom_row int32[m+1] or None, right_col int32[n+1] or None)."""
+    import torch
+    a, b = _u8(a, "a"), _u8(b, "b")
+    n, m = a.numel(), b.numel()
+    if score is None:
+        score = torch.empty(1, dtype=torch.int32, device=a.device)
+    if want_rows and bottom_row is None:
+        bottom_row = torch.empty(m + 1, dtype=torch.int32, device=a.device)
+    if want_cols and right_col is None:
+        right_col = torch.empty(n + 1, dtype=torch.int32, device=a.device)
+    _check(load().paco_affine_align(ctx.handle, _ptr(a), n, _ptr(b), m, _scores(scores), _ptr(score),
+                                    _ptr(bottom_row), _ptr(right_col), _stream(stream)), ctx)
+    return score, bottom_row, right_col
+
+
+def paco_affine_align_host_ptr(ctx: Context, a_ptr, n, b_ptr, m, scores, score_ptr, row_ptr=None, col_ptr=None):
+    """Host-buffer variant on raw host pointers (e.g. pinned tensors)."""
+    _check(load().paco_affine_align_host(ctx.handle, a_ptr, n, b_ptr, m, _scores(scores), score_ptr, row_ptr,
+                                         col_ptr, None), ctx)
+
+
+def paco_affine_batch(ctx: Context, a_cat, b_cat, h_a_off, h_b_off, scores, out=None, stream=None):
+    """Scores of independent pairs: device concatenations, HOST int64 offsets;
+    returns the int32[npairs] score tensor."""
+    import numpy as np
+    import torch
+    h_a_off = np.ascontiguousarray(h_a_off, dtype=np.int64)
+    h_b_off = np.ascontiguousarray(h_b_off, dtype=np.int64)
+    npairs = h_a_off.size - 1
+    if out is None:
+        out = torch.empty(max(npairs, 1), dtype=torch.int32, device=a_cat.device)
+    p = lambda x: x.ctypes.data_as(ctypes.c_void_p)
+    _check(load().paco_affine_batch(ctx.handle, _ptr(a_cat), p(h_a_off), _ptr(b_cat), p(h_b_off), npairs,
+                                    _scores(scores), _ptr(out), _stream(stream)), ctx)
+    return out
 
 
 def paco_lcs_submit(ctx: Context, a, b, want_boundaries=False) -> int:

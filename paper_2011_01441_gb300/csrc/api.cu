@@ -122,6 +122,8 @@ void paco_ctx_destroy(paco_ctx *ctx) {
     serve_shutdown(ctx);
     cudaDeviceSynchronize();
     batch_release(ctx);
+    affine_state_free(ctx->affine);
+    ctx->affine = nullptr;
     for (DevBuf *b : {&ctx->small, &ctx->hbuf, &ctx->lbits, &ctx->rbits, &ctx->rows, &ctx->sums,
                       &ctx->h_a, &ctx->h_b, &ctx->h_top, &ctx->h_left, &ctx->h_row, &ctx->h_col,
                       &ctx->h_len}) {
@@ -178,6 +180,10 @@ int paco_ctx_set_option(paco_ctx *ctx, int option, int64_t value) {
             if (value < 0 || value > (1 << 20)) return PACO_EINVAL;
             ctx->opt_tile_base = value;
             return PACO_OK;
+        case PACO_OPT_AFFINE_ROWS:
+            if (!(value == 0 || value == 2 || value == 4 || value == 8)) return PACO_EINVAL;
+            ctx->opt_affine_rows = (int)value;
+            return PACO_OK;
         case PACO_OPT_TEST_STALL:
             if (value < -1 || value > 0x7fffffff) return PACO_EINVAL;
             ctx->test_stall = (int)value;
@@ -201,6 +207,7 @@ int paco_ctx_get_option(paco_ctx *ctx, int option, int64_t *value) {
         case PACO_OPT_TILES: *value = ctx->opt_tiles; return PACO_OK;
         case PACO_OPT_TILE_BASE: *value = ctx->opt_tile_base; return PACO_OK;
         case PACO_OPT_BATCH_CHUNKS: *value = ctx->last_batch_chunk; return PACO_OK;
+        case PACO_OPT_AFFINE_ROWS: *value = ctx->opt_affine_rows; return PACO_OK;
         case PACO_OPT_TEST_STALL: *value = ctx->test_stall; return PACO_OK;
         default: return PACO_EINVAL;
     }

@@ -20,6 +20,7 @@ namespace paco {
 struct BatchState;
 struct ServeEngine;
 struct TileState;
+struct AffineState;
 
 // A pair plan plus its strip offsets resident on the device.
 struct CachedPairPlan {
@@ -43,6 +44,7 @@ struct paco_ctx {
     int opt_engine = 0, opt_chunk = 0, opt_warps = 0, opt_orient = 0, opt_schedule = 0, opt_wpl = 0;
     int opt_tiles = 0;            // single pair: 0 = strip pipeline, 1..3 = tile schedule (PACO, PA, PO)
     int64_t opt_tile_base = 0;    // tile schedules: smallest tile side in granules (0 = per schedule)
+    int opt_affine_rows = 0;      // affine alignment: rows per lane, 4 or 8 (0 = 4)
     int test_stall = -1;
     int opt_alphabet = 256;
     long long wait_limit_ns = 2000000000LL;
@@ -56,6 +58,7 @@ struct paco_ctx {
     paco::BatchState *batch = nullptr;
     paco::BatchState *recover = nullptr;  // the subsequence recovery's batch engine state
     paco::TileState *tiles = nullptr;     // tile schedules: layouts and buffers
+    paco::AffineState *affine = nullptr;  // affine alignment: band plans and buffers
     paco::ServeEngine *serve = nullptr;
 
     int *err_ptr() { return (int *)small.ptr; }
@@ -84,5 +87,6 @@ void serve_shutdown(paco_ctx *ctx);
 int run_tiles(paco_ctx *ctx, const uint8_t *a, int64_t n, const uint8_t *b, int64_t m, int32_t *bottom_row,
               int32_t *right_col, int32_t *len, cudaStream_t st);
 void tile_state_free(TileState *T);
+void affine_state_free(AffineState *A);
 void batch_release(paco_ctx *ctx);
 }  // namespace paco
