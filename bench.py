@@ -7,7 +7,8 @@ path over that pair: boundary preparation, the strip-pipeline kernel, and the
 two boundary prefixes.  Inputs are resident in HBM before timing; the 256 KB
 of inputs fit in L2, so L2 is flushed (a 512 MiB write) between timed steps.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--config mutated|small|skinny|batch|serve]
+  python bench.py [--gpus N] [--steps K] [--warmup W]
+                 [--config mutated|small|skinny|batch|serve|recover|schedules|affine|affine_batch]
   python bench.py --impl reference ...   # the CPU oracle on a bounded sample
 
 Under torchrun each rank computes its own copy of the workload (independent
@@ -42,6 +43,13 @@ OPS_PER_WORD_STEP = 4
 # add, max, max).  The bit-parallel kernels need only OPS_PER_WORD_STEP per
 # 31 cells, so they can exceed this cell-wise roofline; both are reported.
 CELL_OPS = 4
+# Affine-gap alignment (Gotoh's recurrence, the variant named beside Eq. 1):
+# per cell H - (open + extend) once (shared by the gap to the right and the
+# gap below), E and F each one subtract and one max, the match score one
+# compare and one select, the diagonal add, and the three-way max as two
+# maxes: 10 INT32 lane-ops.
+AFFINE_CELL_OPS = 10
+AFFINE_SCORES = (2, 3, 5, 2)   # match, mismatch, gap open, gap extend
 
 
 def _dist():
@@ -546,6 +554,135 @@ def run_recover_bench(args):
     ctx.close()
 
 
+def cpu_baseline_affine(a, b, scores, budget_s=12.0):
+    """The affine oracle as it stands, single thread, on the first rows of the
+    same pair (a bounded sample), extrapolated to GCUPS."""
+    import oracle
+    oracle.build()
+    probe = min(a.size, 256)
+    t = time.perf_counter()
+    oracle.affine(a[:probe], b, *scores)
+    dt = max(time.perf_counter() - t, 1e-6)
+    rows = int(min(a.size, max(probe, probe * budget_s / dt)))
+    t = time.perf_counter()
+    oracle.affine(a[:rows], b, *scores)
+    dt = time.perf_counter() - t
+    return {"value": rows * b.size / dt / 1e9, "unit": "GCUPS", "cores": 1, "kind": "oracle",
+            "sample": f"first {rows} rows x all {b.size} columns of the same pair ({rows * b.size:.3e} cells, {dt:.1f} s)"}
+
+
+def run_affine_bench(args):
+    """Affine-gap alignment (include/paco_affine.h): the 131072-square mutated
+    pair (config affine) or the 4096-pair batch (config affine_batch), scores
+    match 2, mismatch 3, gap open 5, gap extend 2."""
+    import ctypes
+    import torch
+    import paper_2011_01441_gb300 as P
+    P.load()
+    ctx = P.Context(0)
+    batch = args.config == "affine_batch"
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    S = AFFINE_SCORES
+    if batch:
+        bt = W.batch_pairs()
+        da = torch.from_numpy(bt.a_cat).cuda()
+        db = torch.from_numpy(bt.b_cat).cuda()
+        out = torch.empty(bt.npairs, dtype=torch.int32, device="cuda")
+        cells = bt.cells()
+        desc = "affine-gap alignment, " + bt.name + " (seed 4)"
+
+        def step():
+            P.paco_affine_batch(ctx, da, db, bt.a_off, bt.b_off, S, out=out)
+    else:
+        pair = W.single_mutated()
+        n, m = pair.a.size, pair.b.size
+        da = torch.from_numpy(pair.a).cuda()
+        db = torch.from_numpy(pair.b).cuda()
+        sc = torch.empty(1, dtype=torch.int32, device="cuda")
+        row = torch.empty(m + 1, dtype=torch.int32, device="cuda")
+        col = torch.empty(n + 1, dtype=torch.int32, device="cuda")
+        cells = float(n) * m
+        desc = "affine-gap alignment, pair 131072x131072 sigma=20, 10% subs + 2.5% ins + 2.5% del (seed 2)"
+
+        def step():
+            P.paco_affine_align(ctx, da, db, S, score=sc, bottom_row=row, right_col=col)
+    for _ in range(args.warmup):
+        step()
+    ctx.sync()
+    step_ms, kernel_ms = [], []
+    with ClockSampler(0) as clocks:
+        for _ in range(args.steps):
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            step()
+            e1.record()
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            kernel_ms.append(P.paco_last_kernel_ms(ctx)[0])
+    ctx.sync()
+    value = cells * args.steps / (sum(step_ms) * 1e-3) / 1e9
+    peak_ops = P.paco_measure_int_peak(ctx, 0)
+    kmed = statistics.median(kernel_ms)
+    achieved = cells * AFFINE_CELL_OPS / (kmed * 1e-3)
+    rows = ctx.get_option(P.OPT_AFFINE_ROWS) or 4
+    line = {"metric": METRIC, "value": value, "unit": "GCUPS", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": sum(step_ms) / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": desc, "cells": cells, "scores": dict(zip(("match", "mismatch", "gap_open",
+                                                                             "gap_extend"), S)),
+                       "engine": f"row bands of 32 lanes x {rows} rows, tagged hand-off words",
+                       "l2": "flushed between timed steps (512 MiB write)"},
+            "kernel_ms_median": kmed,
+            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
+                         "unit": f"Tops/s (int32 lane-ops, {AFFINE_CELL_OPS} per cell)", "frac": achieved / peak_ops,
+                         "traffic": _profiled_traffic("k_affine_batch4096_full.md" if batch else "k_affine_pair131072_launches.md",
+                                                      ["affine.cu", "bp_device.cuh"]),
+                         "kernel": "k_affine", "ops_per_cell": AFFINE_CELL_OPS,
+                         "peak_source": "measured: paco_measure_int_peak(op=0), full-rate IADD3 on all SMs"},
+            "gpu_launches": args.steps,
+            "clocks": clocks.summary()}
+    if batch:
+        line["config"]["pairs"] = bt.npairs
+        if not args.no_cpu_baseline:
+            import oracle
+            oracle.build()
+            cores = os.cpu_count() or 1
+            k = min(bt.npairs, 4 * cores)
+            while True:   # grow the sample of pairs until it takes ~10 s on all host cores
+                t0 = time.perf_counter()
+                oracle.affine_batch(bt.a_cat, bt.a_off[:k + 1], bt.b_cat, bt.b_off[:k + 1], S, threads=cores)
+                dt = time.perf_counter() - t0
+                if dt > 5.0 or k == bt.npairs:
+                    break
+                k = min(bt.npairs, int(k * max(2.0, 10.0 / max(dt, 1e-3))))
+            ck = float(np.sum(np.diff(bt.a_off[:k + 1]) * np.diff(bt.b_off[:k + 1])))
+            line["cpu_baseline"] = {"value": ck / dt / 1e9, "unit": "GCUPS", "cores": cores, "kind": "oracle",
+                                    "sample": f"first {k} of {bt.npairs} pairs ({ck:.3e} cells, {dt:.1f} s)"}
+    else:
+        ha = torch.from_numpy(pair.a).pin_memory()
+        hb = torch.from_numpy(pair.b).pin_memory()
+        hrow = torch.empty(m + 1, dtype=torch.int32).pin_memory()
+        hcol = torch.empty(n + 1, dtype=torch.int32).pin_memory()
+        hs = ctypes.c_int32(0)
+        vp = lambda t: ctypes.c_void_p(t.data_ptr())
+        P.paco_affine_align_host_ptr(ctx, vp(ha), n, vp(hb), m, S, ctypes.byref(hs), vp(hrow), vp(hcol))
+        e2e_t = []
+        for _ in range(max(3, args.steps)):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            P.paco_affine_align_host_ptr(ctx, vp(ha), n, vp(hb), m, S, ctypes.byref(hs), vp(hrow), vp(hcol))
+            e2e_t.append(time.perf_counter() - t0)
+        assert hs.value == int(sc.item())
+        line["e2e"] = {"value": cells / statistics.median(e2e_t) / 1e9, "unit": "GCUPS", "h2d_bytes_per_step": n + m,
+                       "d2h_bytes_per_step": 4 * (n + 1) + 4 * (m + 1) + 4}
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline_affine(pair.a, pair.b, S)
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def run_schedules_bench(args):
     """The paper's comparison on one GB300: the 131072-square mutated pair
     under the strip pipeline and under the PACO, PA and PO tile schedules
@@ -604,7 +741,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="mutated", choices=["mutated", "small", "skinny", "batch", "serve", "recover", "schedules"])
+    ap.add_argument("--config", default="mutated", choices=["mutated", "small", "skinny", "batch", "serve", "recover", "schedules",
+                                                               "affine", "affine_batch"])
     ap.add_argument("--requests", type=int, default=3000, help="serving: requests taken from the stream")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="batch: skip the one-pair-per-launch comparison")
@@ -619,6 +757,8 @@ def main():
         run_recover_bench(args)
     elif args.config == "schedules":
         run_schedules_bench(args)
+    elif args.config in ("affine", "affine_batch"):
+        run_affine_bench(args)
     else:
         run_gpu(args)
 

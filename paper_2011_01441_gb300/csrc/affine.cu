@@ -367,6 +367,8 @@ int aff_occupancy(int R) {
 struct AffineState {
     DevBuf jobs, hbuf, flags, offs, degen;
     uint32_t tag = 0;             // tag of the last launch (0: none yet)
+    std::vector<int64_t> key;     // a_off and b_off of the planned layout
+    int plan_rows = 0, njobs = 0, ndegen = 0;
     std::vector<AffJob> h_jobs;
     std::vector<int64_t> h_offs;
 };
@@ -398,86 +400,99 @@ static int run_affine(paco_ctx *ctx, const uint8_t *a_cat, const int64_t *h_a_of
     int R = ctx->opt_affine_rows ? ctx->opt_affine_rows : 4;
     const int band = 32 * R;
 
-    // offsets: a_off, b_off, row_off, col_off (npairs + 1 each)
+    // The plan depends only on the pair lengths and R: a call with the same
+    // layout as the last one reuses the uploaded jobs and offsets.
     const size_t np1 = (size_t)npairs + 1;
-    A->h_offs.assign(4 * np1, 0);
-    int64_t *ao = A->h_offs.data(), *bo = ao + np1, *ro = bo + np1, *co = ro + np1;
-    for (size_t k = 0; k < np1; ++k) {
-        ao[k] = h_a_off[k];
-        bo[k] = h_b_off[k];
-    }
-    std::vector<int32_t> degen;
-    std::vector<int> order;
-    int max_bands = 0;
-    for (int k = 0; k < npairs; ++k) {
-        const int64_t n = ao[k + 1] - ao[k], m = bo[k + 1] - bo[k];
-        ro[k + 1] = ro[k] + m + 1;
-        co[k + 1] = co[k] + n + 1;
-        if (n == 0 || m == 0) {
-            degen.push_back(k);
-        } else {
-            order.push_back(k);
-            max_bands = std::max(max_bands, (int)((n + band - 1) / band));
+    bool same = A->plan_rows == R && A->key.size() == 2 * np1;
+    for (size_t k = 0; same && k < np1; ++k) same = A->key[k] == h_a_off[k] && A->key[np1 + k] == h_b_off[k];
+    cudaError_t e = cudaSuccess;
+    if (!same) {
+        // offsets: a_off, b_off, row_off, col_off (npairs + 1 each)
+        A->h_offs.assign(4 * np1, 0);
+        int64_t *ao = A->h_offs.data(), *bo = ao + np1, *ro = bo + np1, *co = ro + np1;
+        for (size_t k = 0; k < np1; ++k) {
+            ao[k] = h_a_off[k];
+            bo[k] = h_b_off[k];
         }
-    }
-    // bands level by level, larger pairs first within a level: every band
-    // after the band above it
-    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
-        return (ao[x + 1] - ao[x]) * (bo[x + 1] - bo[x]) > (ao[y + 1] - ao[y]) * (bo[y + 1] - bo[y]);
-    });
-    A->h_jobs.clear();
-    std::vector<int> prev_job(npairs, -1);
-    std::vector<int64_t> prev_out(npairs, -1);
-    int64_t hcols = 0;
-    for (int lvl = 0; lvl < max_bands; ++lvl) {
-        for (int k : order) {
+        std::vector<int32_t> degen;
+        std::vector<int> order;
+        int max_bands = 0;
+        for (int k = 0; k < npairs; ++k) {
             const int64_t n = ao[k + 1] - ao[k], m = bo[k + 1] - bo[k];
-            const int64_t r0 = (int64_t)lvl * band;
-            if (r0 >= n) continue;
-            AffJob J{};
-            J.r0 = (int32_t)r0;
-            J.nr = (int32_t)std::min<int64_t>(band, n - r0);
-            J.m = (int32_t)m;
-            J.pair = k;
-            J.a_off = ao[k] + r0;
-            J.b_off = bo[k];
-            J.in_job = prev_job[k];
-            J.in_off = prev_out[k];
-            J.last = r0 + J.nr == n;
-            J.out_off = -1;
-            if (!J.last) {
-                J.out_off = hcols;
-                hcols += m + 1;
+            ro[k + 1] = ro[k] + m + 1;
+            co[k + 1] = co[k] + n + 1;
+            if (n == 0 || m == 0) {
+                degen.push_back(k);
+            } else {
+                order.push_back(k);
+                max_bands = std::max(max_bands, (int)((n + band - 1) / band));
             }
-            prev_job[k] = (int)A->h_jobs.size();
-            prev_out[k] = J.out_off;
-            A->h_jobs.push_back(J);
         }
+        // bands level by level, larger pairs first within a level: every band
+        // after the band above it
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+            return (ao[x + 1] - ao[x]) * (bo[x + 1] - bo[x]) > (ao[y + 1] - ao[y]) * (bo[y + 1] - bo[y]);
+        });
+        A->h_jobs.clear();
+        std::vector<int> prev_job(npairs, -1);
+        std::vector<int64_t> prev_out(npairs, -1);
+        int64_t hcols = 0;
+        for (int lvl = 0; lvl < max_bands; ++lvl) {
+            for (int k : order) {
+                const int64_t n = ao[k + 1] - ao[k], m = bo[k + 1] - bo[k];
+                const int64_t r0 = (int64_t)lvl * band;
+                if (r0 >= n) continue;
+                AffJob J{};
+                J.r0 = (int32_t)r0;
+                J.nr = (int32_t)std::min<int64_t>(band, n - r0);
+                J.m = (int32_t)m;
+                J.pair = k;
+                J.a_off = ao[k] + r0;
+                J.b_off = bo[k];
+                J.in_job = prev_job[k];
+                J.in_off = prev_out[k];
+                J.last = r0 + J.nr == n;
+                J.out_off = -1;
+                if (!J.last) {
+                    J.out_off = hcols;
+                    hcols += m + 1;
+                }
+                prev_job[k] = (int)A->h_jobs.size();
+                prev_out[k] = J.out_off;
+                A->h_jobs.push_back(J);
+            }
+        }
+        const int njobs = (int)A->h_jobs.size();
+        int rc;
+        if ((rc = ensure_bytes(ctx, A->offs, A->h_offs.size() * 8)) != PACO_OK) return rc;
+        if ((rc = ensure_bytes(ctx, A->jobs, std::max<size_t>(1, njobs) * sizeof(AffJob))) != PACO_OK) return rc;
+        if ((rc = ensure_bytes(ctx, A->flags, 16)) != PACO_OK) return rc;
+        if ((rc = ensure_bytes(ctx, A->hbuf, std::max<int64_t>(1, hcols) * 8)) != PACO_OK) return rc;
+        if ((rc = ensure_bytes(ctx, A->degen, std::max<size_t>(1, degen.size()) * 4)) != PACO_OK) return rc;
+        e = cudaMemcpyAsync(A->offs.ptr, A->h_offs.data(), A->h_offs.size() * 8, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && njobs)
+            e = cudaMemcpyAsync(A->jobs.ptr, A->h_jobs.data(), (size_t)njobs * sizeof(AffJob), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && !degen.empty())
+            e = cudaMemcpyAsync(A->degen.ptr, degen.data(), degen.size() * 4, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // pageable staging must be read before reuse
+        if (e != cudaSuccess) return set_cuda_error(ctx, e, "affine plan upload");
+        A->key.assign(h_a_off, h_a_off + np1);
+        A->key.insert(A->key.end(), h_b_off, h_b_off + np1);
+        A->plan_rows = R;
+        A->njobs = njobs;
+        A->ndegen = (int)degen.size();
     }
-    const int njobs = (int)A->h_jobs.size();
-    int rc;
-    if ((rc = ensure_bytes(ctx, A->offs, A->h_offs.size() * 8)) != PACO_OK) return rc;
-    if ((rc = ensure_bytes(ctx, A->jobs, std::max<size_t>(1, njobs) * sizeof(AffJob))) != PACO_OK) return rc;
-    if ((rc = ensure_bytes(ctx, A->flags, 16)) != PACO_OK) return rc;
-    if ((rc = ensure_bytes(ctx, A->hbuf, std::max<int64_t>(1, hcols) * 8)) != PACO_OK) return rc;
-    if ((rc = ensure_bytes(ctx, A->degen, std::max<size_t>(1, degen.size()) * 4)) != PACO_OK) return rc;
-    cudaError_t e = cudaMemcpyAsync(A->offs.ptr, A->h_offs.data(), A->h_offs.size() * 8, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess && njobs)
-        e = cudaMemcpyAsync(A->jobs.ptr, A->h_jobs.data(), (size_t)njobs * sizeof(AffJob), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess && !degen.empty())
-        e = cudaMemcpyAsync(A->degen.ptr, degen.data(), degen.size() * 4, cudaMemcpyHostToDevice, st);
+    const int njobs = A->njobs, ndegen = A->ndegen;
     if (e == cudaSuccess) e = cudaMemsetAsync(A->flags.ptr, 0, 4, st);
     // a new tag per launch; after the 13-bit tag wraps, words of the launch
     // that used the same tag are cleared first
     A->tag = A->tag % kTagMask + 1;
     if (e == cudaSuccess && A->tag == 1) e = cudaMemsetAsync(A->hbuf.ptr, 0, A->hbuf.bytes, st);
-    // pageable staging: the copies above must finish before the vectors change
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return set_cuda_error(ctx, e, "affine plan upload");
+    if (e != cudaSuccess) return set_cuda_error(ctx, e, "affine launch set-up");
     const int64_t *d_off = (const int64_t *)A->offs.ptr;
-    if (!degen.empty()) {
-        k_affine_degenerate<<<std::min<int>((int)degen.size(), 4096), 128, 0, st>>>(
-            (const int32_t *)A->degen.ptr, (int)degen.size(), d_off, d_off + np1, sc.gap_open, sc.gap_extend,
+    if (ndegen) {
+        k_affine_degenerate<<<std::min(ndegen, 4096), 128, 0, st>>>(
+            (const int32_t *)A->degen.ptr, ndegen, d_off, d_off + np1, sc.gap_open, sc.gap_extend,
             d_score, bottom_row, d_off + 2 * np1, right_col, d_off + 3 * np1);
         e = cudaGetLastError();
         if (e != cudaSuccess) return set_cuda_error(ctx, e, "k_affine_degenerate");

@@ -130,6 +130,21 @@ def test_batch_mixed_sizes(ctx, rows_per_lane):
     assert np.array_equal(got.cpu().numpy()[:80], want)
 
 
+def test_batch_plan_reuse_with_new_data(ctx):
+    """Repeated calls with the same lengths reuse the uploaded plan; new
+    symbols in the same layout still give the oracle's scores."""
+    A = [W.symbols(96, k, 100 + 173 * k, 4) for k in range(15)]
+    B = [W.mutate_rate(x, 4, 0.2, 97, k) for k, x in enumerate(A)]
+    a_cat, a_off = _cat(A)
+    b_cat, b_off = _cat(B)
+    for it in range(3):
+        x = a_cat if it % 2 == 0 else (a_cat + it) % 4
+        got = P.paco_affine_batch(ctx, _dev(x), _dev(b_cat), a_off, b_off, SCORES)
+        ctx.sync()
+        want = oracle.affine_batch(x.astype(np.uint8), a_off, b_cat, b_off, SCORES)
+        assert np.array_equal(got.cpu().numpy()[:15], want), it
+
+
 def test_batch_full_workload_4096_pairs(ctx):
     """The 4096-pair workload (lengths log-uniform in [64, 8192], alphabet 4,
     15% mutation) in the configuration the benchmark times: every score
