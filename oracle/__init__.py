@@ -20,13 +20,18 @@ caller-given first row/column, see `lcs_oracle.c`):
   `affine_oracle.c`)
 * `affine_batch(a_cat, a_off, b_cat, b_off, scores, threads)` -> per-pair
   scores
+* `lws(n, d0, kind, T, seed)` -> (D[0..n], argmin[0..n]): the 1D problem of
+  Sec. "PACO 1D" (least weight subsequence) with the weight families of
+  `lws_oracle.c`; `lws_weight(kind, i, j, T, seed)` evaluates one weight
 
 Pins that tie it to something other than itself live in
 `tests/test_oracle_pins.py` (brute-force enumeration, indel distance,
 closed forms, invariants, the CLRS worked example) and
 `tests/test_oracle_affine_pins.py` (enumeration of every alignment, the
 LCS, Levenshtein and indel special cases, gap-block closed forms,
-symmetries).
+symmetries) and `tests/test_oracle_lws_pins.py` (enumeration of every
+subsequence path, Dijkstra of scipy on the same DAG, closed forms of the
+test weight families).
 """
 from __future__ import annotations
 
@@ -41,6 +46,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lcs_oracle.c")
 _SRC_BITPAR = os.path.join(_HERE, "lcs_bitpar.c")
 _SRC_AFFINE = os.path.join(_HERE, "affine_oracle.c")
+_SRC_LWS = os.path.join(_HERE, "lws_oracle.c")
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -48,11 +54,12 @@ _lib = None
 
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (plain C, -O2, no vector intrinsics)."""
-    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_BITPAR), os.path.getmtime(_SRC_AFFINE))
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_BITPAR), os.path.getmtime(_SRC_AFFINE),
+                 os.path.getmtime(_SRC_LWS))
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < newest:
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-pthread",
-                               _SRC, _SRC_BITPAR, _SRC_AFFINE, "-o", tmp])
+                               _SRC, _SRC_BITPAR, _SRC_AFFINE, _SRC_LWS, "-o", tmp])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -77,6 +84,10 @@ def _load():
             lib.oracle_affine.restype = ctypes.c_int
             lib.oracle_affine_batch.argtypes = [P, P, P, P, I64, I64, I64, I64, I64, P, ctypes.c_int]
             lib.oracle_affine_batch.restype = ctypes.c_int
+            lib.oracle_lws.argtypes = [I64, I64, ctypes.c_int, I64, ctypes.c_uint32, P, P]
+            lib.oracle_lws.restype = ctypes.c_int
+            lib.oracle_lws_weight.argtypes = [ctypes.c_int, I64, I64, I64, ctypes.c_uint32]
+            lib.oracle_lws_weight.restype = I64
             _lib = lib
     return _lib
 
@@ -208,3 +219,18 @@ def affine_batch(a_cat, a_off, b_cat, b_off, scores, threads=None):
     if rc != 0:
         raise ValueError(f"oracle_affine_batch failed ({rc})")
     return out
+
+
+def lws(n, d0=0, kind=0, T=40, seed=0):
+    """(D[0..n], argmin[0..n]) of D[j] = min_{i<j} D[i] + w(i, j), D[0] = d0
+    (int64 arrays; argmin = smallest minimising i, argmin[0] = -1)."""
+    D = np.empty(int(n) + 1, dtype=np.int64)
+    arg = np.empty(int(n) + 1, dtype=np.int64)
+    rc = _load().oracle_lws(int(n), int(d0), int(kind), int(T), int(seed) & 0xFFFFFFFF, _ptr(D), _ptr(arg))
+    if rc != 0:
+        raise ValueError(f"oracle_lws failed ({rc})")
+    return D, arg
+
+
+def lws_weight(kind, i, j, T=40, seed=0):
+    return int(_load().oracle_lws_weight(int(kind), int(i), int(j), int(T), int(seed) & 0xFFFFFFFF))
