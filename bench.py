@@ -8,7 +8,7 @@ two boundary prefixes.  Inputs are resident in HBM before timing; the 256 KB
 of inputs fit in L2, so L2 is flushed (a 512 MiB write) between timed steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W]
-                 [--config mutated|small|skinny|batch|serve|recover|schedules|affine|affine_batch]
+                 [--config mutated|small|skinny|batch|serve|recover|schedules|affine|affine_batch|lws]
   python bench.py --impl reference ...   # the CPU oracle on a bounded sample
 
 Under torchrun each rank computes its own copy of the workload (independent
@@ -50,6 +50,13 @@ CELL_OPS = 4
 # maxes: 10 INT32 lane-ops.
 AFFINE_CELL_OPS = 10
 AFFINE_SCORES = (2, 3, 5, 2)   # match, mismatch, gap open, gap extend
+# The 1D problem (Eq. 1D): one term D[i] + w(i, j) and its min is 20 INT32
+# lane-ops with the benchmark weight: the jump deviation, the cap test (two
+# compares) and select, the square, the hash (a multiply, the xor with j and
+# the seed, three shift-xor rounds, two multiplies, the mask), the two adds
+# and the min.
+LWS_TERM_OPS = 20
+LWS_N, LWS_T, LWS_SEED = 131072, 40, 6
 
 
 def _dist():
@@ -683,6 +690,66 @@ def run_affine_bench(args):
     ctx.close()
 
 
+def run_lws_bench(args):
+    """The 1D problem (include/paco_lws.h) for n = 131072, D[0] = 0, weight
+    T = 40, seed 6: every term D[i] + w(i, j), i < j, is one cell."""
+    import torch
+    import paper_2011_01441_gb300 as P
+    P.load()
+    ctx = P.Context(0)
+    n = LWS_N
+    out = torch.empty(n + 1, dtype=torch.int32, device="cuda")
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        P.paco_lws(ctx, n, 0, LWS_T, LWS_SEED, out=out)
+    ctx.sync()
+    step_ms, kernel_ms = [], []
+    with ClockSampler(0) as clocks:
+        for _ in range(args.steps):
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            P.paco_lws(ctx, n, 0, LWS_T, LWS_SEED, out=out)
+            e1.record()
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            kernel_ms.append(P.paco_last_kernel_ms(ctx)[0])
+    ctx.sync()
+    cells = n * (n + 1) / 2
+    value = cells * args.steps / (sum(step_ms) * 1e-3) / 1e9
+    peak_ops = P.paco_measure_int_peak(ctx, 0)
+    kmed = statistics.median(kernel_ms)
+    achieved = cells * LWS_TERM_OPS / (kmed * 1e-3)
+    line = {"metric": METRIC, "value": value, "unit": "GCUPS (terms D[i] + w(i, j) of Eq. 1D per second)",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": sum(step_ms) / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": f"1D problem (least weight subsequence), n={n}, D[0]=0, weight T={LWS_T} seed={LWS_SEED}",
+                       "cells": cells, "engine": "column blocks of 256, left-looking, flags between blocks",
+                       "l2": "flushed between timed steps (512 MiB write)"},
+            "kernel_ms_median": kmed,
+            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
+                         "unit": f"Tops/s (int32 lane-ops, {LWS_TERM_OPS} per term)", "frac": achieved / peak_ops,
+                         "traffic": _profiled_traffic("k_lws_n131072_full.md", ["lws.cu", "bp_device.cuh"]),
+                         "kernel": "k_lws", "ops_per_cell": LWS_TERM_OPS,
+                         "peak_source": "measured: paco_measure_int_peak(op=0), full-rate IADD3 on all SMs"},
+            "gpu_launches": args.steps,
+            "clocks": clocks.summary()}
+    if not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        t0 = time.perf_counter()
+        oracle.lws(8192, 0, 0, LWS_T, LWS_SEED)
+        dt = max(time.perf_counter() - t0, 1e-6)
+        m = int(min(n, 8192 * (10.0 / dt) ** 0.5))
+        t0 = time.perf_counter()
+        oracle.lws(m, 0, 0, LWS_T, LWS_SEED)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": m * (m + 1) / 2 / dt / 1e9, "unit": "GCUPS", "cores": 1, "kind": "oracle",
+                                "sample": f"the first {m} outputs of the same problem ({m * (m + 1) / 2:.3e} terms, {dt:.1f} s)"}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def run_schedules_bench(args):
     """The paper's comparison on one GB300: the 131072-square mutated pair
     under the strip pipeline and under the PACO, PA and PO tile schedules
@@ -742,7 +809,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="mutated", choices=["mutated", "small", "skinny", "batch", "serve", "recover", "schedules",
-                                                               "affine", "affine_batch"])
+                                                               "affine", "affine_batch", "lws"])
     ap.add_argument("--requests", type=int, default=3000, help="serving: requests taken from the stream")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="batch: skip the one-pair-per-launch comparison")
@@ -759,6 +826,8 @@ def main():
         run_schedules_bench(args)
     elif args.config in ("affine", "affine_batch"):
         run_affine_bench(args)
+    elif args.config == "lws":
+        run_lws_bench(args)
     else:
         run_gpu(args)
 

@@ -1,5 +1,5 @@
 """Python binding of the GB300 LCS library (include/paco_lcs.h, include/paco_plan.h,
-include/paco_affine.h).
+include/paco_affine.h, include/paco_lws.h).
 
 Argument marshalling only: every step of the computation runs in the CUDA
 kernels of libpaco_lcs.so.  Device buffers are torch CUDA tensors (torch is
@@ -68,6 +68,10 @@ class PacoAffineScores(ctypes.Structure):
                 ("gap_extend", ctypes.c_int32)]
 
 
+class PacoLwsWeight(ctypes.Structure):
+    _fields_ = [("T", ctypes.c_int32), ("seed", ctypes.c_uint32), ("noise", ctypes.c_int32)]
+
+
 class PacoServeStats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_uint64) for k in
                 ("submitted", "completed", "cells_done", "queued_now", "inflight_now",
@@ -111,6 +115,7 @@ def load():
         "paco_affine_align": ([P, P, I64, P, I64, ctypes.POINTER(PacoAffineScores), P, P, P, P], INT),
         "paco_affine_align_host": ([P, P, I64, P, I64, ctypes.POINTER(PacoAffineScores), P, P, P, P], INT),
         "paco_affine_batch": ([P, P, P, P, P, I32, ctypes.POINTER(PacoAffineScores), P, P], INT),
+        "paco_lws": ([P, I64, I32, ctypes.POINTER(PacoLwsWeight), P, P], INT),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -336,6 +341,18 @@ def paco_affine_batch(ctx: Context, a_cat, b_cat, h_a_off, h_b_off, scores, out=
     p = lambda x: x.ctypes.data_as(ctypes.c_void_p)
     _check(load().paco_affine_batch(ctx.handle, _ptr(a_cat), p(h_a_off), _ptr(b_cat), p(h_b_off), npairs,
                                     _scores(scores), _ptr(out), _stream(stream)), ctx)
+    return out
+
+
+def paco_lws(ctx: Context, n: int, d0: int = 0, T: int = 40, seed: int = 0, noise: bool = True, out=None,
+             stream=None):
+    """D[0..n] of the 1D problem (Eq. 1D) with the weight of include/paco_lws.h;
+    returns an int32[n+1] CUDA tensor."""
+    import torch
+    if out is None:
+        out = torch.empty(int(n) + 1, dtype=torch.int32, device="cuda")
+    w = PacoLwsWeight(int(T), int(seed) & 0xFFFFFFFF, int(bool(noise)))
+    _check(load().paco_lws(ctx.handle, int(n), int(d0), ctypes.byref(w), _ptr(out), _stream(stream)), ctx)
     return out
 
 

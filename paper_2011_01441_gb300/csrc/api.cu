@@ -124,6 +124,8 @@ void paco_ctx_destroy(paco_ctx *ctx) {
     batch_release(ctx);
     affine_state_free(ctx->affine);
     ctx->affine = nullptr;
+    lws_state_free(ctx->lws);
+    ctx->lws = nullptr;
     for (DevBuf *b : {&ctx->small, &ctx->hbuf, &ctx->lbits, &ctx->rbits, &ctx->rows, &ctx->sums,
                       &ctx->h_a, &ctx->h_b, &ctx->h_top, &ctx->h_left, &ctx->h_row, &ctx->h_col,
                       &ctx->h_len}) {

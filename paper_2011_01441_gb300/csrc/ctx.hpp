@@ -21,6 +21,7 @@ struct BatchState;
 struct ServeEngine;
 struct TileState;
 struct AffineState;
+struct LwsState;
 
 // A pair plan plus its strip offsets resident on the device.
 struct CachedPairPlan {
@@ -59,6 +60,7 @@ struct paco_ctx {
     paco::BatchState *recover = nullptr;  // the subsequence recovery's batch engine state
     paco::TileState *tiles = nullptr;     // tile schedules: layouts and buffers
     paco::AffineState *affine = nullptr;  // affine alignment: band plans and buffers
+    paco::LwsState *lws = nullptr;        // 1D problem: block flags
     paco::ServeEngine *serve = nullptr;
 
     int *err_ptr() { return (int *)small.ptr; }
@@ -88,5 +90,6 @@ int run_tiles(paco_ctx *ctx, const uint8_t *a, int64_t n, const uint8_t *b, int6
               int32_t *right_col, int32_t *len, cudaStream_t st);
 void tile_state_free(TileState *T);
 void affine_state_free(AffineState *A);
+void lws_state_free(LwsState *L);
 void batch_release(paco_ctx *ctx);
 }  // namespace paco

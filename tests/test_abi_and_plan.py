@@ -39,7 +39,7 @@ def test_every_declared_symbol_is_exported(lib):
                 "paco_lcs_submit", "paco_lcs_poll", "paco_serve_get_stats",
                 "paco_measure_int_peak", "paco_last_kernel_ms", "paco_plan_partition",
                 "paco_plan_partition_deps", "paco_plan_pair", "paco_affine_align", "paco_affine_align_host",
-                "paco_affine_batch"}
+                "paco_affine_batch", "paco_lws"}
     assert expected <= set(names), expected - set(names)
     for n in names:
         assert hasattr(lib, n), n
