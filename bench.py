@@ -724,7 +724,7 @@ def run_lws_bench(args):
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": sum(step_ms) / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": {"workload": f"1D problem (least weight subsequence), n={n}, D[0]=0, weight T={LWS_T} seed={LWS_SEED}",
-                       "cells": cells, "engine": "column blocks of 256, left-looking, flags between blocks",
+                       "cells": cells, "engine": "blocks of 256: squares as jobs (atomicMin into running minima), triangles by warp sweeps, tagged words between blocks",
                        "l2": "flushed between timed steps (512 MiB write)"},
             "kernel_ms_median": kmed,
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,

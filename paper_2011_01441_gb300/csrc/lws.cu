@@ -2,19 +2,28 @@
 // D[j] = min_{i<j} D[i] + w(i, j).  Block kernel, host launch and the C ABI
 // of include/paco_lws.h.
 //
-// Layout.  The outputs are cut into blocks of kLwsBlock consecutive j; one
-// CTA of kLwsBlock threads owns one block (thread t <-> j = block start + t,
-// its running minimum in a register).  The work of the recurrence is the
-// triangle {(i, j): i < j}; the CTA of block b walks its column of that
-// triangle from the left: for every earlier block a it waits for a's flag,
-// stages a's finished D in shared memory and folds min_i D[i] + w(i, j) into
-// its minima (the square (a, b) of the paper's quadrant structure), then
-// solves its own diagonal triangle in sub-blocks of 32: warp s finishes its
-// 32 values by a sequential sweep over its lanes (a shuffle per value), and
-// the later warps fold those 32 values in before their own turn.  Finished
-// blocks publish D and set a flag with release semantics.  Blocks are taken
-// from an atomic ticket, so a CTA only ever waits for a block held by a
-// running CTA; every wait is bounded.
+// Layout.  The outputs are cut into blocks of kLwsBlock consecutive j (a
+// CTA of kLwsBlock threads works on one block at a time, thread t <-> j =
+// block start + t).  The work of the recurrence is the triangle
+// {(i, j): i < j}, cut into the squares (a, b) of block pairs a < b and the
+// diagonal triangles of the blocks, like the quadrants of the paper's
+// recursion.  Jobs, in the order a CTA takes them from an atomic ticket:
+//
+//   T(0), T(1), S(0, 2), T(2), S(0, 3), S(1, 3), T(3), ...
+//
+// (every job after the jobs it waits for, so a job only ever waits for a
+// running or finished one; the order is computed from the ticket number).
+// S(a, b) folds min_i D[i] + w(i, j) over block a into block b's running
+// minima P[j] with atomicMin and counts itself done.  T(b) waits for its
+// b - 1 squares, folds block b - 1 in itself 32 values at a time as they are
+// finished (so that square overlaps T(b - 1)), then solves its diagonal
+// triangle 32 values at a time: warp s finishes its values by a sequential
+// sweep in which every lane carries the chain D[k] -> D[k+1] itself (the
+// running minimum of lane k + 1 is shuffled a step early), and the later
+// warps fold those 32 values in before their own turn.  Finished values are
+// published as 64-bit words (launch tag in the high half, D in the low
+// half), written and read as single accesses, so a reader can tell them
+// from stale words without fences or flags.  Every wait is bounded.
 #include "../../include/paco_lws.h"
 #include "bp_device.cuh"
 #include "ctx.hpp"
@@ -30,7 +39,8 @@ namespace {
 
 constexpr int kLwsBlock = 256;            // outputs per block = threads per CTA
 constexpr int kLwsWarps = kLwsBlock / 32;
-constexpr int kLwsInf = 0x3fffffff;       // above every D (D < 2^29 + 2^24 + 256 by the argument checks)
+constexpr int kLwsInf = 0x3f3f3f3f;       // above every D (D < 2^29 + 2^24 + 256 by the argument checks);
+                                          // its byte pattern lets a memset fill P
 
 struct LwsArgs {
     int64_t n;
@@ -39,8 +49,12 @@ struct LwsArgs {
     uint32_t seed;
     uint32_t noise_mask;   // 255 or 0
     int32_t *D;            // n + 1 outputs
-    int *flags;            // [0] ticket, [1 + b] block b finished (this launch's tag)
-    int tag;               // nonzero tag of this launch
+    uint64_t *hand;        // n + 1 tagged words (tag << 32 | D)
+    int *P;                // n + 1 running minima from the squares (kLwsInf before launch)
+    int *done;             // per block: squares folded into it (0 before launch)
+    unsigned long long *ticket;
+    int64_t njobs;
+    uint32_t tag;          // nonzero tag of this launch
     int nblocks;
     int *err;
     long long wait_limit_ns;
@@ -62,95 +76,207 @@ static __device__ __forceinline__ int lws_w(int i, int jt, uint32_t js, uint32_t
     return q + (int)(fmix32(((uint32_t)i * 0x9E3779B1u) ^ js) & noise_mask);
 }
 
-static __device__ __forceinline__ int ld_acquire_flag(const int *p) {
+// The hashed byte of w(i, j) alone (js = j ^ seed).
+static __device__ __forceinline__ int lws_noise(int i, uint32_t js, uint32_t noise_mask) {
+    return (int)(fmix32(((uint32_t)i * 0x9E3779B1u) ^ js) & noise_mask);
+}
+
+// Folds the staged values s[0..count) of i0 .. i0 + count - 1 into best.
+// FAR: every jump of the tile is at least 4096 away from T, so the squared
+// term is the constant 2^24 for all of them and is added once.
+template <bool FAR, int COUNT>
+static __device__ __forceinline__ int fold_tile(int best, const int *s, int i0, int jt, uint32_t js,
+                                                uint32_t noise_mask) {
+    if (FAR) {
+        int m = kLwsInf;
+#pragma unroll 8
+        for (int k = 0; k < COUNT; ++k) m = min(m, s[k] + lws_noise(i0 + k, js, noise_mask));
+        return min(best, m + (1 << 24));
+    }
+#pragma unroll 8
+    for (int k = 0; k < COUNT; ++k) best = min(best, s[k] + lws_w(i0 + k, jt, js, noise_mask));
+    return best;
+}
+
+static __device__ __forceinline__ void st_relaxed_u64(uint64_t *p, uint64_t v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Stages `count` finished values starting at word `i0` into s_val: threads
+// t < count load a word each and reload until every word carries `tag`
+// (bounded wait).  CTA-uniform; false on timeout or a raised error.
+static __device__ __noinline__ bool stage_values(const uint64_t *hand, int64_t i0, int count, uint32_t tag,
+                                                 int *err, long long limit, int *s_val, int *s_bad) {
+    const int t = threadIdx.x;
+    uint64_t w = 0;
+    if (t < count) w = dev::ld_relaxed_u64(hand + i0 + t);
+    bool ready = t >= count || (uint32_t)(w >> 32) == tag;
+    if (!__syncthreads_and(ready)) {
+        // poll the stale words; the error word and the clock are looked at
+        // every 32 rounds, and the CTA sleeps between rounds only after 64
+        const uint64_t t0 = dev::global_ns();
+        for (int spin = 1;; ++spin) {
+            if (t == 0 && (spin & 31) == 0) {
+                int bad = 0;
+                if (dev::ld_relaxed_i32(err) != 0) {
+                    bad = 1;
+                } else if ((long long)(dev::global_ns() - t0) > limit) {
+                    dev::raise_error(err, kEtimeout);
+                    bad = 1;
+                }
+                *s_bad = bad;
+            }
+            if (spin > 64) __nanosleep(64);
+            if (!ready) {
+                w = dev::ld_relaxed_u64(hand + i0 + t);
+                ready = (uint32_t)(w >> 32) == tag;
+            }
+            const bool all = __syncthreads_and(ready);   // also orders *s_bad
+            if (all) break;
+            if ((spin & 31) == 0 && *s_bad) return false;
+        }
+    }
+    if (t < count) s_val[t] = (int)(uint32_t)w;
+    __syncthreads();
+    return true;
+}
+
+// Job of ticket x: sets *a (-1 for a triangle) and *b.  Level b >= 1 holds
+// S(0, b) .. S(b - 2, b), T(b) and starts at ticket 1 + b (b - 1) / 2.
+static __device__ __forceinline__ void lws_job(int64_t x, int *a, int *b) {
+    if (x == 0) {
+        *a = -1;
+        *b = 0;
+        return;
+    }
+    int64_t lv = (int64_t)((1.0 + sqrt(8.0 * (double)(x - 1) + 1.0)) * 0.5);
+    while (1 + lv * (lv - 1) / 2 > x) --lv;
+    while (1 + (lv + 1) * lv / 2 <= x) ++lv;
+    const int64_t idx = x - (1 + lv * (lv - 1) / 2);
+    *b = (int)lv;
+    *a = idx < lv - 1 ? (int)idx : -1;
+}
+
+static __device__ __forceinline__ int ld_acquire_i32(const int *p) {
     int v;
     asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
+static __device__ __forceinline__ int ld_relaxed_l2(const int *p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
 
-// Thread 0 waits (bounded) for a block's flag `f` to carry `tag`; the
-// result is CTA-uniform (scalar arguments keep the caller's state in
-// registers).
-static __device__ __noinline__ bool wait_block(const int *f, int tag, int *err, long long limit, int *s_ok) {
+// Thread 0 waits (bounded) until *cnt >= need; CTA-uniform result.
+static __device__ __noinline__ bool wait_count(const int *cnt, int need, int *err, long long limit, int *s_bad) {
     if (threadIdx.x == 0) {
-        int ok = 1;
-        if (ld_acquire_flag(f) != tag) {
+        int bad = 0;
+        if (ld_acquire_i32(cnt) < need) {
             const uint64_t t0 = dev::global_ns();
             for (int spin = 0;; ++spin) {
                 if (spin > 8) __nanosleep(64);
-                if (ld_acquire_flag(f) == tag) break;
+                if (ld_acquire_i32(cnt) >= need) break;
                 if (dev::ld_relaxed_i32(err) != 0) {
-                    ok = 0;
+                    bad = 1;
                     break;
                 }
                 if ((long long)(dev::global_ns() - t0) > limit) {
                     dev::raise_error(err, kEtimeout);
-                    ok = 0;
+                    bad = 1;
                     break;
                 }
             }
         }
-        *s_ok = ok;
+        *s_bad = bad;
     }
     __syncthreads();
-    return *s_ok != 0;
+    return *s_bad == 0;
 }
 
-__global__ void __launch_bounds__(kLwsBlock) k_lws(LwsArgs P) {
+__global__ void __launch_bounds__(kLwsBlock, 3) k_lws(LwsArgs P) {
     __shared__ int s_D[kLwsBlock];
-    __shared__ int s_ticket, s_ok;
+    __shared__ int s_sub[2][32];
+    __shared__ int64_t s_ticket;
+    __shared__ int s_bad;
     const int t = threadIdx.x;
     const int lane = t & 31, warp = t >> 5;
     for (;;) {
-        if (t == 0) s_ticket = atomicAdd(P.flags, 1);
+        // a raised error ends every CTA at its next job
+        if (t == 0) s_ticket = dev::ld_relaxed_i32(P.err) != 0 ? P.njobs : (int64_t)atomicAdd(P.ticket, 1ull);
         __syncthreads();
-        const int b = s_ticket;
+        const int64_t x = s_ticket;
         __syncthreads();
-        if (b >= P.nblocks) return;
+        if (x >= P.njobs) return;
+        int a, b;
+        lws_job(x, &a, &b);
         const int64_t j64 = (int64_t)b * kLwsBlock + t;
         const int j = (int)j64;
         const int jt = j - P.T;
         const uint32_t js = (uint32_t)j ^ P.seed;
-        int best = j == 0 ? P.d0 : kLwsInf;
 
-        // squares (a, b) for every earlier block a
-        for (int a = 0; a < b; ++a) {
-            if (!wait_block(P.flags + 1 + a, P.tag, P.err, P.wait_limit_ns, &s_ok)) return;
-            s_D[t] = P.D[(int64_t)a * kLwsBlock + t];   // blocks below b are full (a < b <= last)
-            __syncthreads();
+        if (a >= 0) {
+            // S(a, b): fold the whole block a (a < b - 1, a full block)
             const int i0 = a * kLwsBlock;
-#pragma unroll 8
-            for (int k = 0; k < kLwsBlock; ++k) best = min(best, s_D[k] + lws_w(i0 + k, jt, js, P.noise_mask));
+            if (!stage_values(P.hand, i0, kLwsBlock, P.tag, P.err, P.wait_limit_ns, s_D, &s_bad)) return;
+            // jumps of this square span [b start - T - (i0 + 255), b end - T - i0]
+            const int64_t dlo = (int64_t)b * kLwsBlock - P.T - (i0 + kLwsBlock - 1);
+            const int64_t dhi = (int64_t)b * kLwsBlock + kLwsBlock - 1 - P.T - i0;
+            const bool far = dlo >= 4096 || dhi <= -4096;
+            const int best = far ? fold_tile<true, kLwsBlock>(kLwsInf, s_D, i0, jt, js, P.noise_mask)
+                                 : fold_tile<false, kLwsBlock>(kLwsInf, s_D, i0, jt, js, P.noise_mask);
+            if (j64 <= P.n) atomicMin(P.P + j64, best);
+            __threadfence();
             __syncthreads();
+            if (t == 0) atomicAdd(P.done + b, 1);
+            continue;
+        }
+
+        // T(b): the squares (a, b), a < b - 1, are in P once all have counted
+        int best = j == 0 ? P.d0 : kLwsInf;
+        if (b >= 2) {
+            if (!wait_count(P.done + b, b - 1, P.err, P.wait_limit_ns, &s_bad)) return;
+            if (j64 <= P.n) best = ld_relaxed_l2(P.P + j64);
+        }
+        // square (b - 1, b), 32 values at a time as T(b - 1) finishes them
+        if (b > 0) {
+            for (int s = 0; s < kLwsWarps; ++s) {
+                const int i0 = (b - 1) * kLwsBlock + 32 * s;
+                int *sv = s_sub[s & 1];
+                if (!stage_values(P.hand, i0, 32, P.tag, P.err, P.wait_limit_ns, sv, &s_bad)) return;
+                best = fold_tile<false, 32>(best, sv, i0, jt, js, P.noise_mask);
+            }
         }
 
         // the diagonal triangle of block b, 32 values at a time
         const int i0 = b * kLwsBlock;
+        // lane l's weight of the jump from its predecessor, w(j - 1, j): the
+        // chain D[k] -> D[k+1] of the sweeps below takes it by one shuffle
+        const int wstep = lws_w(j - 1, jt, js, P.noise_mask);
         for (int s = 0; s < kLwsWarps; ++s) {
             if (warp == s) {
-                // sequential sweep: lane k's minimum is final once lanes < k are folded in
+                // lane k's minimum is final once lanes < k are folded in; every
+                // lane carries D[ib + k] itself, and the running minimum of
+                // lane k + 1 (folded up to D[ib + k - 1]) is shuffled a step early
+                const int ib = i0 + 32 * s;
+                int dk = __shfl_sync(dev::kFull, best, 0);
 #pragma unroll
-                for (int k = 0; k < 32; ++k) {
-                    const int dk = __shfl_sync(dev::kFull, best, k);
-                    if (lane > k) best = min(best, dk + lws_w(i0 + 32 * s + k, jt, js, P.noise_mask));
+                for (int k = 0; k < 31; ++k) {
+                    const int xk = __shfl_sync(dev::kFull, best, k + 1);
+                    const int wk = __shfl_sync(dev::kFull, wstep, k + 1);
+                    if (lane > k) best = min(best, dk + lws_w(ib + k, jt, js, P.noise_mask));
+                    dk = min(xk, dk + wk);
                 }
                 s_D[t] = best;
-                if (j64 <= P.n) P.D[j64] = best;
+                if (j64 <= P.n) {
+                    P.D[j64] = best;
+                    st_relaxed_u64(P.hand + j64, ((uint64_t)P.tag << 32) | (uint32_t)best);
+                }
             }
             __syncthreads();
-            if (warp > s) {
-                const int ib = i0 + 32 * s;
-#pragma unroll 8
-                for (int k = 0; k < 32; ++k) best = min(best, s_D[32 * s + k] + lws_w(ib + k, jt, js, P.noise_mask));
-            }
+            if (warp > s) best = fold_tile<false, 32>(best, s_D + 32 * s, i0 + 32 * s, jt, js, P.noise_mask);
         }
-        // publish: every thread's store is ordered before the flag by the
-        // CTA barrier and thread 0's release fence
         __syncthreads();
-        if (t == 0) {
-            __threadfence();
-            asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(P.flags + 1 + b), "r"(P.tag) : "memory");
-        }
     }
 }
 
@@ -158,13 +284,14 @@ __global__ void __launch_bounds__(kLwsBlock) k_lws(LwsArgs P) {
 
 // Scratch of the 1D path, owned by the context.
 struct LwsState {
-    DevBuf flags;
-    int tag = 0;   // tag of the last launch (0: none yet)
+    DevBuf ticket, hand, part, done;
+    uint32_t tag = 0;   // tag of the last launch (0: none yet)
 };
 
 void lws_state_free(LwsState *L) {
     if (!L) return;
-    if (L->flags.ptr) cudaFree(L->flags.ptr);
+    for (DevBuf *d : {&L->ticket, &L->hand, &L->part, &L->done})
+        if (d->ptr) cudaFree(d->ptr);
     delete L;
 }
 
@@ -182,14 +309,19 @@ extern "C" int paco_lws(paco_ctx *ctx, int64_t n, int32_t d0, const paco_lws_wei
     LwsState *L = ctx->lws;
     if (!L) return PACO_ENOMEM;
     const int nblocks = (int)((n + 1 + kLwsBlock - 1) / kLwsBlock);
-    int rc = ensure_bytes(ctx, L->flags, ((size_t)nblocks + 1) * sizeof(int));
+    int rc = ensure_bytes(ctx, L->ticket, 16);
+    if (rc == PACO_OK) rc = ensure_bytes(ctx, L->hand, ((size_t)n + 1) * sizeof(uint64_t));
+    if (rc == PACO_OK) rc = ensure_bytes(ctx, L->part, ((size_t)n + 1) * sizeof(int));
+    if (rc == PACO_OK) rc = ensure_bytes(ctx, L->done, (size_t)nblocks * sizeof(int));
     if (rc != PACO_OK) return rc;
-    // a new tag per launch; flags of older launches never match it (the
-    // buffer is cleared when the tag wraps, and zeroed when it grows)
-    L->tag = L->tag >= (1 << 30) ? 1 : L->tag + 1;
+    // a new tag per launch: words of older launches never carry it (the
+    // buffer is zeroed when it grows and cleared when the tag wraps)
+    L->tag = L->tag == 0xffffffffu ? 1u : L->tag + 1u;
     cudaError_t e = cudaSuccess;
-    if (L->tag == 1) e = cudaMemsetAsync(L->flags.ptr, 0, L->flags.bytes, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(L->flags.ptr, 0, sizeof(int), st);  // ticket
+    if (L->tag == 1) e = cudaMemsetAsync(L->hand.ptr, 0, L->hand.bytes, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(L->ticket.ptr, 0, sizeof(int64_t), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(L->part.ptr, 0x3f, ((size_t)n + 1) * sizeof(int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(L->done.ptr, 0, (size_t)nblocks * sizeof(int), st);
     if (e != cudaSuccess) return set_cuda_error(ctx, e, "lws set-up");
     LwsArgs P{};
     P.n = n;
@@ -198,7 +330,11 @@ extern "C" int paco_lws(paco_ctx *ctx, int64_t n, int32_t d0, const paco_lws_wei
     P.seed = w->seed;
     P.noise_mask = w->noise ? 255u : 0u;
     P.D = d_D;
-    P.flags = (int *)L->flags.ptr;
+    P.hand = (uint64_t *)L->hand.ptr;
+    P.ticket = (unsigned long long *)L->ticket.ptr;
+    P.P = (int *)L->part.ptr;
+    P.done = (int *)L->done.ptr;
+    P.njobs = 1 + (int64_t)nblocks * (nblocks - 1) / 2;
     P.tag = L->tag;
     P.nblocks = nblocks;
     P.err = ctx->err_ptr();
@@ -206,7 +342,7 @@ extern "C" int paco_lws(paco_ctx *ctx, int64_t n, int32_t d0, const paco_lws_wei
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lws, kLwsBlock, 0);
     if (e != cudaSuccess) return set_cuda_error(ctx, e, "lws occupancy");
-    const int grid = std::min(nblocks, ctx->sms * std::max(per_sm, 1));
+    const int grid = (int)std::min<int64_t>(P.njobs, (int64_t)ctx->sms * std::max(per_sm, 1));
     cudaEventRecord(ctx->ev0, st);
     k_lws<<<grid, kLwsBlock, 0, st>>>(P);
     e = cudaGetLastError();
