@@ -77,6 +77,29 @@ int paco_plan_tiles(int64_t n, int64_t m, int32_t p, int32_t kind, int64_t base,
                     int64_t cap, int64_t *count, int64_t *dep_off, int64_t *dep_idx, int64_t cap_idx,
                     int64_t *n_idx, int64_t *critical_cells);
 
+/* PACO 1D (Sec. "PACO 1D"): the work of Eq. (1D) over outputs and inputs
+ * 0..n is the triangle {(i, j): i < j}.  The recursion on an output range
+ * runs the left half's triangle, the square updating the right half from
+ * the left half, and the right half's triangle; each square is cut along
+ * its longer side in the ratio floor(p'/2) : ceil(p'/2) together with its
+ * processor list of p' processors, down to one processor per rectangle.
+ * A cut along the input side gives the second part temporary space (one
+ * value per output column of the part) merged by a min after the phase.
+ * Triangles at most `base` wide are base cases on processor 0.
+ * Task kinds: 0 = base triangle (outputs [j0, j1), inputs i < j in the same
+ * range), 1 = rectangle (outputs [j0, j1) x inputs [i0, i1)).  Tasks of one
+ * phase run concurrently; phases run in order.  merge_group = -1 when the
+ * rectangle writes the outputs, else the temporary buffer it writes. */
+typedef struct paco_1d_task {
+    int64_t j0, j1, i0, i1;
+    int32_t proc, phase, merge_group, kind;
+} paco_1d_task;
+
+/* Writes up to `cap` tasks in order, the task count, the number of phases
+ * and the temporary words the input-side cuts need.  Returns 0 or -1. */
+int paco_plan_1d(int64_t n, int32_t p, int64_t base, paco_1d_task *out, int64_t cap, int64_t *count,
+                 int32_t *phases, int64_t *temp_words);
+
 #ifdef __cplusplus
 }
 #endif

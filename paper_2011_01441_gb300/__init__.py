@@ -68,6 +68,12 @@ class PacoAffineScores(ctypes.Structure):
                 ("gap_extend", ctypes.c_int32)]
 
 
+class Paco1dTask(ctypes.Structure):
+    _fields_ = [("j0", ctypes.c_int64), ("j1", ctypes.c_int64), ("i0", ctypes.c_int64), ("i1", ctypes.c_int64),
+                ("proc", ctypes.c_int32), ("phase", ctypes.c_int32), ("merge_group", ctypes.c_int32),
+                ("kind", ctypes.c_int32)]
+
+
 class PacoLwsWeight(ctypes.Structure):
     _fields_ = [("T", ctypes.c_int32), ("seed", ctypes.c_uint32), ("noise", ctypes.c_int32)]
 
@@ -116,6 +122,7 @@ def load():
         "paco_affine_align_host": ([P, P, I64, P, I64, ctypes.POINTER(PacoAffineScores), P, P, P, P], INT),
         "paco_affine_batch": ([P, P, P, P, P, I32, ctypes.POINTER(PacoAffineScores), P, P], INT),
         "paco_lws": ([P, I64, I32, ctypes.POINTER(PacoLwsWeight), P, P], INT),
+        "paco_plan_1d": ([I64, I32, I64, P, I64, ctypes.POINTER(I64), ctypes.POINTER(I32), ctypes.POINTER(I64)], INT),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -354,6 +361,20 @@ def paco_lws(ctx: Context, n: int, d0: int = 0, T: int = 40, seed: int = 0, nois
     w = PacoLwsWeight(int(T), int(seed) & 0xFFFFFFFF, int(bool(noise)))
     _check(load().paco_lws(ctx.handle, int(n), int(d0), ctypes.byref(w), _ptr(out), _stream(stream)), ctx)
     return out
+
+
+def paco_plan_1d(n: int, p: int, base: int):
+    """The PACO 1D partition (include/paco_plan.h): dict with `tasks` (list of
+    dicts j0, j1, i0, i1, proc, phase, merge_group, kind), `phases`, `temp_words`."""
+    L = load()
+    cnt, ph, tw = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int64()
+    if L.paco_plan_1d(int(n), int(p), int(base), None, 0, ctypes.byref(cnt), ctypes.byref(ph), ctypes.byref(tw)) != 0:
+        raise ValueError("paco_plan_1d failed")
+    arr = (Paco1dTask * max(1, cnt.value))()
+    L.paco_plan_1d(int(n), int(p), int(base), ctypes.cast(arr, ctypes.c_void_p), cnt.value, ctypes.byref(cnt),
+                   ctypes.byref(ph), ctypes.byref(tw))
+    tasks = [{f: getattr(arr[k], f) for f, _ in Paco1dTask._fields_} for k in range(cnt.value)]
+    return {"tasks": tasks, "phases": ph.value, "temp_words": tw.value}
 
 
 def paco_lcs_submit(ctx: Context, a, b, want_boundaries=False) -> int:

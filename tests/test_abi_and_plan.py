@@ -39,7 +39,7 @@ def test_every_declared_symbol_is_exported(lib):
                 "paco_lcs_submit", "paco_lcs_poll", "paco_serve_get_stats",
                 "paco_measure_int_peak", "paco_last_kernel_ms", "paco_plan_partition",
                 "paco_plan_partition_deps", "paco_plan_pair", "paco_affine_align", "paco_affine_align_host",
-                "paco_affine_batch", "paco_lws"}
+                "paco_affine_batch", "paco_lws", "paco_plan_1d"}
     assert expected <= set(names), expected - set(names)
     for n in names:
         assert hasattr(lib, n), n
@@ -219,3 +219,101 @@ def test_tile_schedule_critical_paths_follow_the_paper():
     assert 1.95 < pa < 2.05
     assert paco < pa
     assert po > pa
+
+
+# ---------------------------------------------------------------- PACO 1D
+
+def _w1d(i, j, T=40, seed=6):
+    """The benchmark weight of the 1D problem on int64 arrays (its definition)."""
+    d = j - i - T
+    q = np.where(np.abs(d) < 4096, d * d, 1 << 24)
+    h = (((i * 0x9E3779B1) & 0xFFFFFFFF) ^ j ^ seed) & 0xFFFFFFFF
+    h ^= h >> 16
+    h = (h * 0x85EBCA6B) & 0xFFFFFFFF
+    h ^= h >> 13
+    h = (h * 0xC2B2AE35) & 0xFFFFFFFF
+    h ^= h >> 16
+    return q + (h & 255)
+
+
+@pytest.mark.parametrize("n,p,base", [(100, 3, 8), (255, 4, 16), (1000, 7, 32), (513, 1, 64), (2000, 152, 64),
+                                      (64, 16, 2)])
+def test_plan_1d_covers_the_triangle_once(lib, n, p, base):
+    r = P.paco_plan_1d(n, p, base)
+    cover = np.zeros((n + 1, n + 1), dtype=np.int32)   # [i, j]
+    for t in r["tasks"]:
+        assert 0 <= t["proc"] < p
+        if t["kind"] == 0:
+            blk = cover[t["j0"]:t["j1"], t["j0"]:t["j1"]]
+            blk += np.triu(np.ones_like(blk), k=1)
+        else:
+            assert t["i1"] <= t["j0"]                  # a square reads finished inputs only
+            cover[t["i0"]:t["i1"], t["j0"]:t["j1"]] += 1
+    assert np.array_equal(cover, np.triu(np.ones((n + 1, n + 1), dtype=np.int32), k=1))
+    if p == 1:
+        assert r["temp_words"] == 0 and all(t["merge_group"] == -1 for t in r["tasks"])
+
+
+@pytest.mark.parametrize("n,p", [(4095, 4), (4095, 16), (4095, 64), (4095, 3), (4095, 152), (8191, 7)])
+def test_plan_1d_square_balance_and_half_perimeters(lib, n, p):
+    """Every square is split into p rectangles of area 1/p of it (up to the
+    rounding of one row or column per cut), and the rectangles of the top
+    square have half-perimeters O(side / sqrt(p)) (Theorem of Sec. "PACO 1D")."""
+    r = P.paco_plan_1d(n, p, 64)
+    by_phase = defaultdict(list)
+    for t in r["tasks"]:
+        if t["kind"] == 1:
+            by_phase[t["phase"]].append(t)
+    for ph, rects in by_phase.items():
+        w = max(t["j1"] for t in rects) - min(t["j0"] for t in rects)
+        h = max(t["i1"] for t in rects) - min(t["i0"] for t in rects)
+        areas = Counter()
+        for t in rects:
+            areas[t["proc"]] += (t["j1"] - t["j0"]) * (t["i1"] - t["i0"])
+        assert sum(areas.values()) == w * h
+        cuts = int(np.ceil(np.log2(p))) + 1
+        for a in areas.values():
+            assert abs(a - w * h / p) <= cuts * (w + h), (ph, a, w * h / p)
+    top = max(by_phase.values(), key=lambda rs: sum((t["j1"] - t["j0"]) * (t["i1"] - t["i0"]) for t in rs))
+    side = max(t["j1"] for t in top) - min(t["j0"] for t in top)
+    for t in top:
+        hp = (t["j1"] - t["j0"]) + (t["i1"] - t["i0"])
+        assert hp <= 4 * side / np.sqrt(p) + 2, (hp, side, p)
+    if p & (p - 1) == 0:   # a power of two: alternating halvings give equal rectangles
+        assert len({((t["j1"] - t["j0"]), (t["i1"] - t["i0"])) for t in top}) <= 2
+    # temporary space of the input-side cuts: O(sqrt(p) n log n)
+    assert r["temp_words"] <= 4 * np.sqrt(p) * (n + 1) * np.log2(n + 1)
+
+
+@pytest.mark.parametrize("n,p,base", [(300, 5, 16), (777, 8, 40)])
+def test_plan_1d_schedule_computes_eq_1d(lib, n, p, base):
+    """Running the plan phase by phase (rectangles of a phase into the
+    outputs or into their temporary buffers, merged by a min after the
+    phase) gives the oracle's D: the order respects every dependency."""
+    import oracle
+    r = P.paco_plan_1d(n, p, base)
+    D = np.full(n + 1, np.iinfo(np.int64).max // 4, dtype=np.int64)
+    D[0] = 0
+    by_phase = defaultdict(list)
+    for t in r["tasks"]:
+        by_phase[t["phase"]].append(t)
+    for ph in sorted(by_phase):
+        temps = {}
+        for t in by_phase[ph]:
+            if t["kind"] == 0:
+                for j in range(max(t["j0"], 1), t["j1"]):
+                    i = np.arange(t["j0"], j)
+                    if i.size:
+                        D[j] = min(D[j], int(np.min(D[i] + _w1d(i, j))))
+            else:
+                i = np.arange(t["i0"], t["i1"])[:, None]
+                j = np.arange(t["j0"], t["j1"])[None, :]
+                c = np.min(D[i] + _w1d(i, j), axis=0)
+                if t["merge_group"] < 0:
+                    D[t["j0"]:t["j1"]] = np.minimum(D[t["j0"]:t["j1"]], c)
+                else:
+                    temps[(t["merge_group"], t["j0"])] = (t["j0"], c)
+        for j0, c in temps.values():
+            D[j0:j0 + c.size] = np.minimum(D[j0:j0 + c.size], c)
+    Do, _ = oracle.lws(n, 0, 0, 40, 6)
+    assert np.array_equal(D, Do)
