@@ -117,8 +117,10 @@ enum paco_option {
                                    granules (0 = 4 for PACO, 16 for PO) */
     PACO_OPT_AFFINE_ROWS = 12,  /* affine alignment (include/paco_affine.h): rows per
                                    lane of a row band, 2, 4 or 8 (0 = 4) */
-    PACO_OPT_TEST_STALL = 100   /* tests only: make one strip wait on a flag
-                                   nothing sets (exercises the bounded wait) */
+    PACO_OPT_TEST_STALL = 100   /* tests only: make one strip (pair kernel), one
+                                   band job (affine) or one block (1D problem) wait
+                                   for input that never arrives (exercises the
+                                   bounded wait) */
 };
 
 /* ---- single pair ------------------------------------------------------ */

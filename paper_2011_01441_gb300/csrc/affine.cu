@@ -75,6 +75,7 @@ struct AffArgs {
     int gm, gx, go, ge;
     uint32_t tag;             // tag of this launch, 1 .. kTagMask
     long long wait_limit_ns;
+    int stall_job;            // tests: job whose input words never carry the tag (-1: none)
 };
 
 // Word of a band's last row at one column: bits 0..31 H, bits 32..50
@@ -138,11 +139,12 @@ static __device__ __noinline__ Settled settle_slow(const uint64_t *src, bool nee
 
 // Makes sure every word of a chunk loaded earlier carries this launch's tag;
 // false on timeout or a raised error.  Warp-uniform.
-static __device__ __forceinline__ bool settle_chunk(const AffArgs &P, const AffJob &J, int col, ChunkIn &c) {
+static __device__ __forceinline__ bool settle_chunk(const AffArgs &P, const AffJob &J, int col, ChunkIn &c,
+                                                    uint32_t want) {
     const bool need = J.in_job >= 0 && (threadIdx.x & 31) < kAffChunk && col <= J.m;
-    const bool ready = !need || (uint32_t)(c.w >> kTagShift) == P.tag;
+    const bool ready = !need || (uint32_t)(c.w >> kTagShift) == want;
     if (__all_sync(dev::kFull, ready)) return true;
-    const Settled r = settle_slow(P.hbuf + J.in_off + col, need, c.w, P.tag, P.err, P.wait_limit_ns);
+    const Settled r = settle_slow(P.hbuf + J.in_off + col, need, c.w, want, P.err, P.wait_limit_ns);
     c.w = r.w;
     return r.ok != 0;
 }
@@ -260,10 +262,13 @@ static __device__ __forceinline__ void affine_band(const AffArgs &P, const AffJo
     }
     uint64_t *out = J.last ? nullptr : P.hbuf + J.out_off;
     OutChunk o{kNeg, kNeg};
+    // the tag the band's input words must carry (a value no word carries
+    // for the test-only stalled job)
+    const uint32_t want = jid == P.stall_job ? kTagMask + 1 : P.tag;
 
     // chunk 0 settled into the stage, chunk 1 loading into registers
     ChunkIn cur = load_chunk(P, J, lane);
-    if (!settle_chunk(P, J, lane, cur)) return;
+    if (!settle_chunk(P, J, lane, cur, want)) return;
     if (lane < kAffChunk) stage[0][lane] = band_input(P, J, lane, cur);
     cur = load_chunk(P, J, kAffChunk + lane);
     __syncwarp();
@@ -274,7 +279,7 @@ static __device__ __forceinline__ void affine_band(const AffArgs &P, const AffJo
         if (c > 0) {
             flush_out(P, J, o, lane, (c - 1) * kAffChunk, T, out);
             const int col = c * kAffChunk + lane;
-            if (!settle_chunk(P, J, col, cur)) return;
+            if (!settle_chunk(P, J, col, cur, want)) return;
             __syncwarp();
             if (lane < kAffChunk) stage[c & 1][lane] = band_input(P, J, col, cur);
             cur = load_chunk(P, J, col + kAffChunk);
@@ -293,7 +298,7 @@ static __device__ __forceinline__ void affine_band(const AffArgs &P, const AffJo
             flush_out(P, J, o, lane, t - kAffChunk, T, out);
             const int c = t / kAffChunk;
             const int col = c * kAffChunk + lane;
-            if (!settle_chunk(P, J, col, cur)) return;
+            if (!settle_chunk(P, J, col, cur, want)) return;
             __syncwarp();
             if (lane < kAffChunk) stage[c & 1][lane] = band_input(P, J, col, cur);
             cur = load_chunk(P, J, col + kAffChunk);
@@ -517,6 +522,7 @@ static int run_affine(paco_ctx *ctx, const uint8_t *a_cat, const int64_t *h_a_of
         P.go = sc.gap_open;
         P.ge = sc.gap_extend;
         P.wait_limit_ns = ctx->wait_limit_ns;
+        P.stall_job = ctx->test_stall;
         // The bands of one pair form one chain whose pace is its slowest
         // band's, so a single pair gets one CTA per SM (one band per warp
         // scheduler); independent pairs fill every resident slot.

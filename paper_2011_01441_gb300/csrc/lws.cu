@@ -58,6 +58,7 @@ struct LwsArgs {
     int nblocks;
     int *err;
     long long wait_limit_ns;
+    int stall_block;       // tests: block whose triangle waits for words that never come (-1: none)
 };
 
 static __device__ __forceinline__ uint32_t fmix32(uint32_t h) {
@@ -243,7 +244,8 @@ __global__ void __launch_bounds__(kLwsBlock, 3) k_lws(LwsArgs P) {
             for (int s = 0; s < kLwsWarps; ++s) {
                 const int i0 = (b - 1) * kLwsBlock + 32 * s;
                 int *sv = s_sub[s & 1];
-                if (!stage_values(P.hand, i0, 32, P.tag, P.err, P.wait_limit_ns, sv, &s_bad)) return;
+                const uint32_t want = b == P.stall_block ? P.tag ^ 0x80000000u : P.tag;
+                if (!stage_values(P.hand, i0, 32, want, P.err, P.wait_limit_ns, sv, &s_bad)) return;
                 best = fold_tile<false, 32>(best, sv, i0, jt, js, P.noise_mask);
             }
         }
@@ -339,6 +341,7 @@ extern "C" int paco_lws(paco_ctx *ctx, int64_t n, int32_t d0, const paco_lws_wei
     P.nblocks = nblocks;
     P.err = ctx->err_ptr();
     P.wait_limit_ns = ctx->wait_limit_ns;
+    P.stall_block = ctx->test_stall;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lws, kLwsBlock, 0);
     if (e != cudaSuccess) return set_cuda_error(ctx, e, "lws occupancy");

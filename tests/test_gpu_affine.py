@@ -220,3 +220,22 @@ def test_host_buffer_entry_point(ctx):
     P.paco_affine_align_host_ptr(ctx, vp(a), a.size, vp(b), b.size, SCORES, ctypes.byref(s), vp(row), vp(col))
     so, ro, co = oracle.affine(a, b, *SCORES)
     assert s.value == so and np.array_equal(row, ro) and np.array_equal(col, co)
+
+
+def test_bounded_wait_times_out_and_recovers(ctx):
+    """A band whose input never arrives (test-only switch) ends the launch
+    with PACO_ETIMEOUT within the wait limit, not a hang; the context then
+    aligns correctly again."""
+    a = W.symbols(103, 0, 5000, 4)
+    b = W.mutate_rate(a, 4, 0.2, 104, 0)
+    ctx.set_option(P.OPT_WAIT_LIMIT_NS, 50_000_000)
+    ctx.set_option(P.OPT_TEST_STALL, 3)
+    try:
+        with pytest.raises(P.PacoError) as e:
+            P.paco_affine_align(ctx, _dev(a), _dev(b), SCORES)
+            ctx.sync()
+        assert e.value.status == P.PACO_ETIMEOUT
+    finally:
+        ctx.set_option(P.OPT_TEST_STALL, -1)
+        ctx.set_option(P.OPT_WAIT_LIMIT_NS, 2_000_000_000)
+    _check(ctx, a, b, SCORES)

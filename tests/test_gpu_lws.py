@@ -100,3 +100,20 @@ def test_full_size_closed_form_without_noise(ctx):
             cost = r * (q + 1 - T) ** 2 + (kk - r) * (q - T) ** 2
             best = cost if best is None else min(best, cost)
         assert D[j] == best, j
+
+
+def test_bounded_wait_times_out_and_recovers(ctx):
+    """A block whose inputs never arrive (test-only switch) ends the launch
+    with PACO_ETIMEOUT within the wait limit, not a hang; the context then
+    computes correctly again."""
+    ctx.set_option(P.OPT_WAIT_LIMIT_NS, 50_000_000)
+    ctx.set_option(P.OPT_TEST_STALL, 5)
+    try:
+        with pytest.raises(P.PacoError) as e:
+            P.paco_lws(ctx, 3000, 0, 40, 1)
+            ctx.sync()
+        assert e.value.status == P.PACO_ETIMEOUT
+    finally:
+        ctx.set_option(P.OPT_TEST_STALL, -1)
+        ctx.set_option(P.OPT_WAIT_LIMIT_NS, 2_000_000_000)
+    assert np.array_equal(_gpu(ctx, 3000, 0, 40, 1), oracle.lws(3000, 0, 0, 40, 1)[0])
