@@ -9,10 +9,11 @@
 // independent of each other; each takes (H, F, symbol) of the row above from
 // the previous step: from its own registers, from the lane above by one
 // shuffle, or, for the band's first row, from a 16-column staging buffer in
-// shared memory.  A band's last row publishes one 64-bit word per column to
-// global memory: H, H - F and the launch's tag, written and read as single
-// 64-bit accesses, so the band below can tell a published word from a stale
-// one without fences or flags.  The band below loads the words of the next
+// shared memory.  The band's last row is parked in shared memory by its
+// lane, one predicated store per step, and published once per 16 steps as
+// one 64-bit word per column in global memory: H, H - F and the launch's
+// tag, written and read as single 64-bit accesses, so the band below can
+// tell a published word from a stale one without fences or flags.  The band below loads the words of the next
 // 16 columns one chunk ahead and checks their tags when it stages them.
 // Bands are jobs taken from an atomic ticket in an order in which every band
 // comes after the band above it, so a band only ever waits for a running one.
@@ -36,9 +37,6 @@ namespace {
 // +-2^29 by the argument checks) with room to subtract scores for the few
 // hundred steps a row runs before its first column.
 constexpr int kNeg = -(1 << 30);
-#ifndef AFF_DPX
-#define AFF_DPX 0
-#endif
 constexpr int kAffChunk = 16;           // columns per staging chunk of a band's first row
 constexpr int kAffWarps = 4;            // warps per CTA (independent job takers)
 constexpr int kNoSym = -1;              // column symbol outside [1, m]: never equal
@@ -197,15 +195,9 @@ static __device__ __forceinline__ void band_step(BandState<R> &S, const int4 in,
         const int fu = k ? S.F[k - 1] : fu0;   // F[i-1][j]
         const int bu = k ? S.B[k - 1] : bu0;   // symbol of column j
         const int s = S.as[k] == bu ? gm : -gx;
-#if AFF_DPX
-        const int e = __viaddmax_s32(S.E[k], -ge, S.G[k]);
-        const int f = __viaddmax_s32(fu, -ge, gu);
-        const int h = __vimax3_s32(S.D[k] + s, e, f);
-#else
         const int e = max(S.E[k] - ge, S.G[k]);
         const int f = max(fu - ge, gu);
         const int h = max(max(S.D[k] + s, e), f);
-#endif
         S.D[k] = hu;
         S.E[k] = e;
         S.F[k] = f;
@@ -216,20 +208,11 @@ static __device__ __forceinline__ void band_step(BandState<R> &S, const int4 in,
     }
 }
 
-// The band's last row, gathered over a chunk of steps: lane u holds (H, F)
-// of step base + u, i.e. column base + u - (nr - 1).
+// The band's last row over a chunk of steps: lane u holds (H, F) of step
+// base + u, i.e. column base + u - (nr - 1).
 struct OutChunk {
     int h, f;
 };
-template <int R, int KL>
-static __device__ __forceinline__ void gather_out(const BandState<R> &S, OutChunk &o, int lane, int last_lane, int u) {
-    const int hv = __shfl_sync(dev::kFull, S.H[KL], last_lane);
-    const int fv = __shfl_sync(dev::kFull, S.F[KL], last_lane);
-    if (lane == u) {
-        o.h = hv;
-        o.f = fv;
-    }
-}
 
 // Publish the gathered chunk whose first step is `base` (steps below T).
 static __device__ __forceinline__ void flush_out(const AffArgs &P, const AffJob &J, const OutChunk &o, int lane,
@@ -246,7 +229,8 @@ static __device__ __forceinline__ void flush_out(const AffArgs &P, const AffJob 
 }
 
 template <int R, int KL>
-static __device__ __forceinline__ void affine_band(const AffArgs &P, const AffJob &J, int jid, int4 (*stage)[kAffChunk]) {
+static __device__ __forceinline__ void affine_band(const AffArgs &P, const AffJob &J, int jid, int4 (*stage)[kAffChunk],
+                                                   int2 *sout) {
     const int lane = threadIdx.x & 31;
     const int m = J.m, nr = J.nr;
     const int gm = P.gm, gx = P.gx, ge = P.ge, goe = P.go + P.ge;
@@ -262,6 +246,12 @@ static __device__ __forceinline__ void affine_band(const AffArgs &P, const AffJo
     }
     uint64_t *out = J.last ? nullptr : P.hbuf + J.out_off;
     OutChunk o{kNeg, kNeg};
+    // the last row's lane parks (H, F) of step u in the warp's shared slot
+    // u (one predicated store per step); lanes 0..15 take them at the
+    // chunk's end
+    const bool is_last = lane == last_lane;
+#define COLLECT(u) do { if (is_last) sout[u] = make_int2(S.H[KL], S.F[KL]); } while (0)
+#define GATHER() do { __syncwarp(); if (lane < kAffChunk) { const int2 v = sout[lane]; o.h = v.x; o.f = v.y; } __syncwarp(); } while (0)
     // the tag the band's input words must carry (a value no word carries
     // for the test-only stalled job)
     const uint32_t want = jid == P.stall_job ? kTagMask + 1 : P.tag;
@@ -277,6 +267,7 @@ static __device__ __forceinline__ void affine_band(const AffArgs &P, const AffJo
     const int hot = (m / kAffChunk) * kAffChunk;   // steps before `hot` never reach column m
     for (int c = 0; c * kAffChunk < hot; ++c) {
         if (c > 0) {
+            GATHER();
             flush_out(P, J, o, lane, (c - 1) * kAffChunk, T, out);
             const int col = c * kAffChunk + lane;
             if (!settle_chunk(P, J, col, cur, want)) return;
@@ -289,12 +280,13 @@ static __device__ __forceinline__ void affine_band(const AffArgs &P, const AffJo
 #pragma unroll
         for (int u = 0; u < kAffChunk; ++u) {
             band_step<R, false>(S, st[u], c * kAffChunk + u, lane, m, gm, gx, ge, goe);
-            gather_out<R, KL>(S, o, lane, last_lane, u);
+            COLLECT(u);
         }
     }
     for (int t = hot; t < T; ++t) {
         const int u = t % kAffChunk;
         if (u == 0 && t > 0) {
+            GATHER();
             flush_out(P, J, o, lane, t - kAffChunk, T, out);
             const int c = t / kAffChunk;
             const int col = c * kAffChunk + lane;
@@ -305,9 +297,12 @@ static __device__ __forceinline__ void affine_band(const AffArgs &P, const AffJo
             __syncwarp();
         }
         band_step<R, true>(S, stage[(t / kAffChunk) & 1][u], t, lane, m, gm, gx, ge, goe);
-        gather_out<R, KL>(S, o, lane, last_lane, u);
+        COLLECT(u);
     }
+    GATHER();
     flush_out(P, J, o, lane, ((T - 1) / kAffChunk) * kAffChunk, T, out);
+#undef COLLECT
+#undef GATHER
     if (P.right_col) {
         const int64_t base = P.col_off[J.pair] + J.r0 + 1;
 #pragma unroll
@@ -322,6 +317,7 @@ static __device__ __forceinline__ void affine_band(const AffArgs &P, const AffJo
 template <int R>
 __global__ void __launch_bounds__(32 * kAffWarps) k_affine(AffArgs P) {
     __shared__ int4 stage[kAffWarps][2][kAffChunk];
+    __shared__ int2 sout[kAffWarps][kAffChunk];
     const int w = threadIdx.x >> 5;
     for (;;) {
         int jid = 0;
@@ -330,14 +326,14 @@ __global__ void __launch_bounds__(32 * kAffWarps) k_affine(AffArgs P) {
         if (jid >= P.njobs) return;
         const AffJob J = P.jobs[jid];
         switch ((J.nr - 1) % R) {
-            case 0: affine_band<R, 0>(P, J, jid, stage[w]); break;
-            case 1: affine_band<R, 1>(P, J, jid, stage[w]); break;
-            case 2: if (R > 2) affine_band<R, (R > 2 ? 2 : 0)>(P, J, jid, stage[w]); break;
-            case 3: if (R > 3) affine_band<R, (R > 3 ? 3 : 0)>(P, J, jid, stage[w]); break;
-            case 4: if (R > 4) affine_band<R, (R > 4 ? 4 : 0)>(P, J, jid, stage[w]); break;
-            case 5: if (R > 5) affine_band<R, (R > 5 ? 5 : 0)>(P, J, jid, stage[w]); break;
-            case 6: if (R > 6) affine_band<R, (R > 6 ? 6 : 0)>(P, J, jid, stage[w]); break;
-            case 7: if (R > 7) affine_band<R, (R > 7 ? 7 : 0)>(P, J, jid, stage[w]); break;
+            case 0: affine_band<R, 0>(P, J, jid, stage[w], sout[w]); break;
+            case 1: affine_band<R, 1>(P, J, jid, stage[w], sout[w]); break;
+            case 2: if (R > 2) affine_band<R, (R > 2 ? 2 : 0)>(P, J, jid, stage[w], sout[w]); break;
+            case 3: if (R > 3) affine_band<R, (R > 3 ? 3 : 0)>(P, J, jid, stage[w], sout[w]); break;
+            case 4: if (R > 4) affine_band<R, (R > 4 ? 4 : 0)>(P, J, jid, stage[w], sout[w]); break;
+            case 5: if (R > 5) affine_band<R, (R > 5 ? 5 : 0)>(P, J, jid, stage[w], sout[w]); break;
+            case 6: if (R > 6) affine_band<R, (R > 6 ? 6 : 0)>(P, J, jid, stage[w], sout[w]); break;
+            case 7: if (R > 7) affine_band<R, (R > 7 ? 7 : 0)>(P, J, jid, stage[w], sout[w]); break;
         }
     }
 }
