@@ -39,6 +39,9 @@ namespace {
 
 constexpr int kLwsBlock = 256;            // outputs per block = threads per CTA
 constexpr int kLwsWarps = kLwsBlock / 32;
+constexpr int kLwsMaxSms = 1024;          // entries of the per-SM busy counters (a power of two)
+constexpr long long kLwsYieldNs = 50000;  // longest a square waits for a triangle job on its SM
+constexpr size_t kLwsWeightBytes = (size_t)kLwsWarps * 2 * 32 * 32 * sizeof(int);   // 64 KB
 constexpr int kLwsInf = 0x3f3f3f3f;       // above every D (D < 2^29 + 2^24 + 256 by the argument checks);
                                           // its byte pattern lets a memset fill P
 
@@ -52,6 +55,7 @@ struct LwsArgs {
     uint64_t *hand;        // n + 1 tagged words (tag << 32 | D)
     int *P;                // n + 1 running minima from the squares (kLwsInf before launch)
     int *done;             // per block: squares folded into it (0 before launch)
+    int *busy;             // per SM: triangle jobs running their chain part (0 before launch)
     unsigned long long *ticket;
     int64_t njobs;
     uint32_t tag;          // nonzero tag of this launch
@@ -142,6 +146,41 @@ static __device__ __noinline__ bool stage_values(const uint64_t *hand, int64_t i
     return true;
 }
 
+// Like stage_values for a word w each thread t < count loaded earlier:
+// checks the tags, reloads the stale words (bounded wait) and stages the
+// values into s_val.  CTA-uniform; false on timeout or a raised error.
+static __device__ __noinline__ bool settle_values(const uint64_t *hand, int64_t i0, int count, uint32_t tag,
+                                                  int *err, long long limit, uint64_t w, int *s_val, int *s_bad) {
+    const int t = threadIdx.x;
+    bool ready = t >= count || (uint32_t)(w >> 32) == tag;
+    if (!__syncthreads_and(ready)) {
+        const uint64_t t0 = dev::global_ns();
+        for (int spin = 1;; ++spin) {
+            if (t == 0 && (spin & 31) == 0) {
+                int bad = 0;
+                if (dev::ld_relaxed_i32(err) != 0) {
+                    bad = 1;
+                } else if ((long long)(dev::global_ns() - t0) > limit) {
+                    dev::raise_error(err, kEtimeout);
+                    bad = 1;
+                }
+                *s_bad = bad;
+            }
+            if (spin > 64) __nanosleep(64);
+            if (!ready) {
+                w = dev::ld_relaxed_u64(hand + i0 + t);
+                ready = (uint32_t)(w >> 32) == tag;
+            }
+            const bool all = __syncthreads_and(ready);   // also orders *s_bad
+            if (all) break;
+            if ((spin & 31) == 0 && *s_bad) return false;
+        }
+    }
+    if (t < count) s_val[t] = (int)(uint32_t)w;
+    __syncthreads();
+    return true;
+}
+
 // Job of ticket x: sets *a (-1 for a triangle) and *b.  Level b >= 1 holds
 // S(0, b) .. S(b - 2, b), T(b) and starts at ticket 1 + b (b - 1) / 2.
 static __device__ __forceinline__ void lws_job(int64_t x, int *a, int *b) {
@@ -156,6 +195,12 @@ static __device__ __forceinline__ void lws_job(int64_t x, int *a, int *b) {
     const int64_t idx = x - (1 + lv * (lv - 1) / 2);
     *b = (int)lv;
     *a = idx < lv - 1 ? (int)idx : -1;
+}
+
+static __device__ __forceinline__ int smid() {
+    int v;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(v));
+    return v;
 }
 
 static __device__ __forceinline__ int ld_acquire_i32(const int *p) {
@@ -196,6 +241,7 @@ static __device__ __noinline__ bool wait_count(const int *cnt, int need, int *er
 }
 
 __global__ void __launch_bounds__(kLwsBlock, 3) k_lws(LwsArgs P) {
+    extern __shared__ int s_wts[];   // per warp: [2][32 k][32 lanes] weights of the triangle
     __shared__ int s_D[kLwsBlock];
     __shared__ int s_sub[2][32];
     __shared__ int64_t s_ticket;
@@ -217,7 +263,18 @@ __global__ void __launch_bounds__(kLwsBlock, 3) k_lws(LwsArgs P) {
         const uint32_t js = (uint32_t)j ^ P.seed;
 
         if (a >= 0) {
-            // S(a, b): fold the whole block a (a < b - 1, a full block)
+            // S(a, b): fold the whole block a (a < b - 1, a full block).  A
+            // square yields its SM while a triangle job there runs its part of
+            // the chain (at most kLwsYieldNs): the chain sets the pace.
+            if (t == 0) {
+                const int *bz = P.busy + (smid() & (kLwsMaxSms - 1));
+                if (dev::ld_relaxed_i32(bz) > 0) {
+                    const uint64_t t0 = dev::global_ns();
+                    while (dev::ld_relaxed_i32(bz) > 0 && (long long)(dev::global_ns() - t0) < kLwsYieldNs)
+                        __nanosleep(256);
+                }
+            }
+            __syncthreads();
             const int i0 = a * kLwsBlock;
             if (!stage_values(P.hand, i0, kLwsBlock, P.tag, P.err, P.wait_limit_ns, s_D, &s_bad)) return;
             // jumps of this square span [b start - T - (i0 + 255), b end - T - i0]
@@ -233,25 +290,46 @@ __global__ void __launch_bounds__(kLwsBlock, 3) k_lws(LwsArgs P) {
             continue;
         }
 
-        // T(b): the squares (a, b), a < b - 1, are in P once all have counted
+        // T(b).  First, while the inputs are still coming: each lane's weights
+        // of its own warp's 32 values (the sweep) and of the warp before's 32
+        // values (the fold on the triangle's critical path), into this lane's
+        // column of the warp's shared tables.
+        const int i0 = b * kLwsBlock;
+        {
+            int *sw = s_wts + warp * (2 * 32 * 32);
+            const int ib = i0 + 32 * warp;
+#pragma unroll 4
+            for (int k = 0; k < 32; ++k) {
+                sw[k * 32 + lane] = lws_w(ib + k, jt, js, P.noise_mask);
+                sw[32 * 32 + k * 32 + lane] = lws_w(ib - 32 + k, jt, js, P.noise_mask);
+            }
+        }
+        // the squares (a, b), a < b - 1, are in P once all have counted
         int best = j == 0 ? P.d0 : kLwsInf;
         if (b >= 2) {
             if (!wait_count(P.done + b, b - 1, P.err, P.wait_limit_ns, &s_bad)) return;
             if (j64 <= P.n) best = ld_relaxed_l2(P.P + j64);
         }
-        // square (b - 1, b), 32 values at a time as T(b - 1) finishes them
+        int *bz = P.busy + (smid() & (kLwsMaxSms - 1));
+        if (t == 0) atomicAdd(bz, 1);
+        // square (b - 1, b), 32 values at a time as T(b - 1) finishes them;
+        // the words of the next 32 are loaded before this 32 are folded, so
+        // a word is mostly checked after it has arrived
         if (b > 0) {
+            const uint32_t want = b == P.stall_block ? P.tag ^ 0x80000000u : P.tag;
+            const int64_t h0 = (int64_t)(b - 1) * kLwsBlock;
+            uint64_t pre = t < 32 ? dev::ld_relaxed_u64(P.hand + h0 + t) : 0;
             for (int s = 0; s < kLwsWarps; ++s) {
                 const int i0 = (b - 1) * kLwsBlock + 32 * s;
                 int *sv = s_sub[s & 1];
-                const uint32_t want = b == P.stall_block ? P.tag ^ 0x80000000u : P.tag;
-                if (!stage_values(P.hand, i0, 32, want, P.err, P.wait_limit_ns, sv, &s_bad)) return;
+                if (!settle_values(P.hand, h0 + 32 * s, 32, want, P.err, P.wait_limit_ns, pre, sv, &s_bad)) return;
+                if (s + 1 < kLwsWarps && t < 32) pre = dev::ld_relaxed_u64(P.hand + h0 + 32 * (s + 1) + t);
                 best = fold_tile<false, 32>(best, sv, i0, jt, js, P.noise_mask);
             }
         }
 
         // the diagonal triangle of block b, 32 values at a time
-        const int i0 = b * kLwsBlock;
+        const int *sw = s_wts + warp * (2 * 32 * 32) + lane;
         // lane l's weight of the jump from its predecessor, w(j - 1, j): the
         // chain D[k] -> D[k+1] of the sweeps below takes it by one shuffle
         const int wstep = lws_w(j - 1, jt, js, P.noise_mask);
@@ -266,7 +344,7 @@ __global__ void __launch_bounds__(kLwsBlock, 3) k_lws(LwsArgs P) {
                 for (int k = 0; k < 31; ++k) {
                     const int xk = __shfl_sync(dev::kFull, best, k + 1);
                     const int wk = __shfl_sync(dev::kFull, wstep, k + 1);
-                    if (lane > k) best = min(best, dk + lws_w(ib + k, jt, js, P.noise_mask));
+                    if (lane > k) best = min(best, dk + sw[k * 32]);
                     dk = min(xk, dk + wk);
                 }
                 s_D[t] = best;
@@ -276,9 +354,15 @@ __global__ void __launch_bounds__(kLwsBlock, 3) k_lws(LwsArgs P) {
                 }
             }
             __syncthreads();
-            if (warp > s) best = fold_tile<false, 32>(best, s_D + 32 * s, i0 + 32 * s, jt, js, P.noise_mask);
+            if (warp == s + 1) {   // the next sweep's warp: its weights are in the table
+#pragma unroll 8
+                for (int k = 0; k < 32; ++k) best = min(best, s_D[32 * s + k] + sw[32 * 32 + k * 32]);
+            } else if (warp > s + 1) {
+                best = fold_tile<false, 32>(best, s_D + 32 * s, i0 + 32 * s, jt, js, P.noise_mask);
+            }
         }
         __syncthreads();
+        if (t == 0) atomicSub(bz, 1);
     }
 }
 
@@ -286,13 +370,13 @@ __global__ void __launch_bounds__(kLwsBlock, 3) k_lws(LwsArgs P) {
 
 // Scratch of the 1D path, owned by the context.
 struct LwsState {
-    DevBuf ticket, hand, part, done;
+    DevBuf ticket, hand, part, done, busy;
     uint32_t tag = 0;   // tag of the last launch (0: none yet)
 };
 
 void lws_state_free(LwsState *L) {
     if (!L) return;
-    for (DevBuf *d : {&L->ticket, &L->hand, &L->part, &L->done})
+    for (DevBuf *d : {&L->ticket, &L->hand, &L->part, &L->done, &L->busy})
         if (d->ptr) cudaFree(d->ptr);
     delete L;
 }
@@ -315,6 +399,7 @@ extern "C" int paco_lws(paco_ctx *ctx, int64_t n, int32_t d0, const paco_lws_wei
     if (rc == PACO_OK) rc = ensure_bytes(ctx, L->hand, ((size_t)n + 1) * sizeof(uint64_t));
     if (rc == PACO_OK) rc = ensure_bytes(ctx, L->part, ((size_t)n + 1) * sizeof(int));
     if (rc == PACO_OK) rc = ensure_bytes(ctx, L->done, (size_t)nblocks * sizeof(int));
+    if (rc == PACO_OK) rc = ensure_bytes(ctx, L->busy, (size_t)kLwsMaxSms * sizeof(int));
     if (rc != PACO_OK) return rc;
     // a new tag per launch: words of older launches never carry it (the
     // buffer is zeroed when it grows and cleared when the tag wraps)
@@ -324,6 +409,7 @@ extern "C" int paco_lws(paco_ctx *ctx, int64_t n, int32_t d0, const paco_lws_wei
     if (e == cudaSuccess) e = cudaMemsetAsync(L->ticket.ptr, 0, sizeof(int64_t), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(L->part.ptr, 0x3f, ((size_t)n + 1) * sizeof(int), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(L->done.ptr, 0, (size_t)nblocks * sizeof(int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(L->busy.ptr, 0, (size_t)kLwsMaxSms * sizeof(int), st);
     if (e != cudaSuccess) return set_cuda_error(ctx, e, "lws set-up");
     LwsArgs P{};
     P.n = n;
@@ -336,6 +422,7 @@ extern "C" int paco_lws(paco_ctx *ctx, int64_t n, int32_t d0, const paco_lws_wei
     P.ticket = (unsigned long long *)L->ticket.ptr;
     P.P = (int *)L->part.ptr;
     P.done = (int *)L->done.ptr;
+    P.busy = (int *)L->busy.ptr;
     P.njobs = 1 + (int64_t)nblocks * (nblocks - 1) / 2;
     P.tag = L->tag;
     P.nblocks = nblocks;
@@ -343,11 +430,13 @@ extern "C" int paco_lws(paco_ctx *ctx, int64_t n, int32_t d0, const paco_lws_wei
     P.wait_limit_ns = ctx->wait_limit_ns;
     P.stall_block = ctx->test_stall;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lws, kLwsBlock, 0);
+    e = cudaFuncSetAttribute(k_lws, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLwsWeightBytes);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lws, kLwsBlock, kLwsWeightBytes);
     if (e != cudaSuccess) return set_cuda_error(ctx, e, "lws occupancy");
     const int grid = (int)std::min<int64_t>(P.njobs, (int64_t)ctx->sms * std::max(per_sm, 1));
     cudaEventRecord(ctx->ev0, st);
-    k_lws<<<grid, kLwsBlock, 0, st>>>(P);
+    k_lws<<<grid, kLwsBlock, kLwsWeightBytes, st>>>(P);
     e = cudaGetLastError();
     cudaEventRecord(ctx->ev1, st);
     if (e != cudaSuccess) return set_cuda_error(ctx, e, "k_lws");
