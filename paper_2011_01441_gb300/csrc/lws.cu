@@ -322,7 +322,10 @@ __global__ void __launch_bounds__(kLwsBlock, 3) k_lws(LwsArgs P) {
             for (int s = 0; s < kLwsWarps; ++s) {
                 const int i0 = (b - 1) * kLwsBlock + 32 * s;
                 int *sv = s_sub[s & 1];
-                if (!settle_values(P.hand, h0 + 32 * s, 32, want, P.err, P.wait_limit_ns, pre, sv, &s_bad)) return;
+                if (!settle_values(P.hand, h0 + 32 * s, 32, want, P.err, P.wait_limit_ns, pre, sv, &s_bad)) {
+                    if (t == 0) atomicSub(bz, 1);
+                    return;
+                }
                 if (s + 1 < kLwsWarps && t < 32) pre = dev::ld_relaxed_u64(P.hand + h0 + 32 * (s + 1) + t);
                 best = fold_tile<false, 32>(best, sv, i0, jt, js, P.noise_mask);
             }
