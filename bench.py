@@ -218,28 +218,73 @@ def cpu_baseline_pair(a, b, budget_s=12.0):
             "sample": f"first {rows} rows x all {b.size} columns of the same pair ({rows * b.size:.3e} cells, {dt:.1f} s)"}
 
 
+def _reference_step(config, budget_s):
+    """One bounded sample of the oracle on the host cores for `config`:
+    (result dict like cpu_baseline, workload description, unit)."""
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    if config in ("mutated", "small", "skinny"):
+        pair, desc = _workload(config)
+        return cpu_baseline_pair(pair.a, pair.b, budget_s=budget_s), desc, "GCUPS"
+    if config == "affine":
+        pair = W.single_mutated()
+        return (cpu_baseline_affine(pair.a, pair.b, AFFINE_SCORES, budget_s=budget_s),
+                "affine-gap alignment, pair 131072x131072 sigma=20, 10% subs + 2.5% ins + 2.5% del (seed 2)", "GCUPS")
+    if config == "lws":
+        t0 = time.perf_counter()
+        oracle.lws(4096, 0, 0, LWS_T, LWS_SEED)
+        dt = max(time.perf_counter() - t0, 1e-6)
+        m = int(min(LWS_N, 4096 * (budget_s / dt) ** 0.5))
+        t0 = time.perf_counter()
+        oracle.lws(m, 0, 0, LWS_T, LWS_SEED)
+        dt = time.perf_counter() - t0
+        return ({"value": m * (m + 1) / 2 / dt / 1e9, "unit": "GCUPS", "cores": 1, "kind": "oracle",
+                 "sample": f"the first {m} outputs of the same problem ({m * (m + 1) / 2:.3e} terms, {dt:.1f} s)"},
+                f"1D problem (least weight subsequence), n={LWS_N}, D[0]=0, weight T={LWS_T} seed={LWS_SEED}",
+                "GCUPS (terms D[i] + w(i, j) of Eq. 1D per second)")
+    # the batch workloads: the first k pairs, spread over the host cores
+    bt = W.batch_pairs()
+    affine = config == "affine_batch"
+    k = min(bt.npairs, 4 * cores)
+    while True:
+        t0 = time.perf_counter()
+        if affine:
+            oracle.affine_batch(bt.a_cat, bt.a_off[:k + 1], bt.b_cat, bt.b_off[:k + 1], AFFINE_SCORES, threads=cores)
+        else:
+            oracle.lcs_batch(bt.a_cat, bt.a_off[:k + 1], bt.b_cat, bt.b_off[:k + 1], threads=cores, boundaries=False)
+        dt = time.perf_counter() - t0
+        if dt > budget_s / 2 or k == bt.npairs:
+            break
+        k = min(bt.npairs, int(k * max(2.0, budget_s / max(dt, 1e-3))))
+    ck = float(np.sum(np.diff(bt.a_off[:k + 1]) * np.diff(bt.b_off[:k + 1])))
+    desc = ("affine-gap alignment, " if affine else "") + bt.name + " (seed 4)"
+    return ({"value": ck / dt / 1e9, "unit": "GCUPS", "cores": cores, "kind": "oracle",
+             "sample": f"first {k} of {bt.npairs} pairs ({ck:.3e} cells, {dt:.1f} s)"}, desc, "GCUPS")
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
         return
-    pair, desc = _workload(args.config)
+    cfg = args.config if args.config in ("mutated", "small", "skinny", "affine", "affine_batch", "lws") else "batch"
     for _ in range(args.warmup):
-        cpu_baseline_pair(pair.a, pair.b, budget_s=1.0)
+        _reference_step(cfg, 1.0)
     vals = []
     t0 = time.perf_counter()
-    last = None
+    last = desc = unit = None
     for _ in range(args.steps):
-        last = cpu_baseline_pair(pair.a, pair.b, budget_s=max(2.0, 40.0 / max(1, args.steps)))
+        last, desc, unit = _reference_step(cfg, max(2.0, 40.0 / max(1, args.steps)))
         vals.append(last["value"])
     el = time.perf_counter() - t0
     v = statistics.median(vals)
-    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GCUPS", "n_gpus": args.gpus,
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": unit, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic", "config": {"workload": desc, "l2": "n/a (CPU)"},
-            "cpu_baseline": {"value": v, "unit": "GCUPS", "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": v, "unit": last["unit"], "cores": last["cores"], "kind": "oracle",
                              "sample": last["sample"]},
-            "e2e": {"value": v, "unit": "GCUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "e2e": {"value": v, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
