@@ -110,12 +110,22 @@ def _workload(name):
 
 
 class ClockSampler:
-    """nvidia-smi clocks/throttle reasons sampled during the timed region."""
+    """nvidia-smi clocks/throttle reasons sampled during the timed region.
+
+    nvidia-smi is started on entry and the region only begins once its first
+    sample has arrived; each sample is stamped with its arrival time, and
+    the summary keeps the samples that arrived inside the region (plus one
+    sampling period after it, for the sample that covers the region's end).
+    A region shorter than the sampling period may hold none: then the first
+    sample after the region began stands in and `in_region` says so."""
+
+    PERIOD_MS = 50
 
     def __init__(self, index=0):
         self.index = index
         self.proc = None
-        self.lines = []
+        self.lines = []   # (arrival time, csv line)
+        self.t_in = self.t_out = None
 
     def __enter__(self):
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -123,45 +133,62 @@ class ClockSampler:
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", str(self.PERIOD_MS)],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
+            t0 = time.monotonic()
+            while not self.lines and time.monotonic() - t0 < 5.0 and self.proc.poll() is None:
+                time.sleep(0.005)
         except Exception:
             self.proc = None
+        self.t_in = time.monotonic()
         return self
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.monotonic(), line.strip()))
 
     def __exit__(self, *exc):
+        self.t_out = time.monotonic()
         if self.proc is not None:
+            time.sleep(self.PERIOD_MS * 1.5e-3)
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
             except Exception:
                 self.proc.kill()
 
-    def summary(self):
-        sm, mx, reasons = [], None, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            f = [x.strip() for x in ln.split(",")]
-            if len(f) < 9:
-                continue
-            try:
-                sm.append(float(f[1]))
-                mx = float(f[2])
-            except ValueError:
-                continue
-            for nm, v in zip(names, f[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(nm)
-        if not sm:
+    @staticmethod
+    def _parse(line):
+        f = [x.strip() for x in line.split(",")]
+        if len(f) < 9:
             return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+        try:
+            sm, mx = float(f[1]), float(f[2])
+        except ValueError:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        return sm, mx, {nm for nm, v in zip(names, f[5:9]) if v.lower().startswith("active")}
+
+    def summary(self):
+        if self.t_in is None:
+            return None
+        t_end = (self.t_out if self.t_out is not None else time.monotonic()) + self.PERIOD_MS * 1e-3
+        parsed = [(t, self._parse(ln)) for t, ln in self.lines]
+        parsed = [(t, r) for t, r in parsed if r is not None]
+        inside = [r for t, r in parsed if self.t_in <= t <= t_end]
+        in_region = bool(inside)
+        if not inside:
+            after = [r for t, r in parsed if t >= self.t_in]
+            inside = after[:1]
+        if not inside:
+            return None
+        reasons = set().union(*(r[2] for r in inside))
+        return {"sm_mhz": statistics.median(r[0] for r in inside), "sm_max_mhz": inside[-1][1],
+                "reasons": sorted(reasons), "samples": len(inside), "in_region": in_region,
+                "period_ms": self.PERIOD_MS,
+                "region_ms": round(((self.t_out or time.monotonic()) - self.t_in) * 1e3, 1)}
 
 
 def _peaks():
@@ -316,6 +343,7 @@ def run_gpu(args):
     ctx.sync()
     kernel_ms = []
     step_ms = []
+    host_us = []  # host time of the call itself: cached plan + launches, no wait on the GPU
     _barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clocks:
@@ -324,7 +352,9 @@ def run_gpu(args):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
+            h0 = time.perf_counter()
             step()
+            host_us.append((time.perf_counter() - h0) * 1e6)
             e1.record(stream)
             e1.synchronize()
             step_ms.append(e0.elapsed_time(e1))
@@ -382,6 +412,8 @@ def run_gpu(args):
                    "words_per_lane": plan.get("words_per_lane", 1),
                    "l2": "flushed between timed steps (512 MiB write)"},
         "kernel_ms_median": kmed,
+        "kernel_ms_min": min(kernel_ms),
+        "host_call_us_median": statistics.median(host_us),
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                      "unit": "Tops/s (int32 lane-ops, 4 per cell)", "frac": achieved / peak_ops,
                      "traffic": traffic, "kernel": "k_pair_bp", "ops_per_cell": CELL_OPS,
@@ -465,6 +497,7 @@ def run_batch_bench(args):
             "config": {"workload": bt.name + " (seed 4)", "pairs": bt.npairs, "cells": cells,
                        "engine": "batch graph, warp jobs", "alphabet": 4, "chunk_by_class": _chunks_by_class(ctx.get_option(P.OPT_BATCH_CHUNKS)),
                        "l2": "flushed between timed steps"},
+            "step_ms_median": med, "step_ms_min": min(ms),
             "plain_one_pair_per_launch": None if args.no_plain else
             {"value": cells / plain_s / 1e9, "unit": "GCUPS", "seconds": plain_s},
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
@@ -685,7 +718,7 @@ def run_affine_bench(args):
                                                                              "gap_extend"), S)),
                        "engine": f"row bands of 32 lanes x {rows} rows, tagged hand-off words",
                        "l2": "flushed between timed steps (512 MiB write)"},
-            "kernel_ms_median": kmed,
+            "kernel_ms_median": kmed, "kernel_ms_min": min(kernel_ms),
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                          "unit": f"Tops/s (int32 lane-ops, {AFFINE_CELL_OPS} per cell)", "frac": achieved / peak_ops,
                          "traffic": _profiled_traffic("k_affine_batch4096_full.md" if batch else "k_affine_pair131072_launches.md",
@@ -771,7 +804,7 @@ def run_lws_bench(args):
             "config": {"workload": f"1D problem (least weight subsequence), n={n}, D[0]=0, weight T={LWS_T} seed={LWS_SEED}",
                        "cells": cells, "engine": "blocks of 256: squares as jobs (atomicMin into running minima), triangles by warp sweeps, tagged words between blocks",
                        "l2": "flushed between timed steps (512 MiB write)"},
-            "kernel_ms_median": kmed,
+            "kernel_ms_median": kmed, "kernel_ms_min": min(kernel_ms),
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                          "unit": f"Tops/s (int32 lane-ops, {LWS_TERM_OPS} per term)", "frac": achieved / peak_ops,
                          "traffic": _profiled_traffic("k_lws_n131072_full.md", ["lws.cu", "bp_device.cuh"]),
@@ -847,10 +880,17 @@ def run_schedules_bench(args):
     ctx.close()
 
 
+# Default timed steps per workload: about half a second of GPU work, so that
+# the clock sampler sees several samples inside the timed region.
+DEFAULT_STEPS = {"mutated": 200, "small": 2000, "skinny": 200, "batch": 1000, "affine": 20,
+                 "affine_batch": 60, "lws": 60}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: about half a second of GPU work per workload; 10 for the reference arm)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="mutated", choices=["mutated", "small", "skinny", "batch", "serve", "recover", "schedules",
@@ -859,6 +899,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="batch: skip the one-pair-per-launch comparison")
     args = ap.parse_args()
+    if args.steps is None:
+        args.steps = 10 if args.impl == "reference" else DEFAULT_STEPS.get(args.config, 10)
     if args.impl == "reference":
         run_reference(args)
     elif args.config == "batch":

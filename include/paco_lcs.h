@@ -159,8 +159,8 @@ int paco_lcs_boundaries_host(paco_ctx *ctx, const uint8_t *a, int64_t n,
  * in the paper; this is a deployment variant of paco_lcs_boundaries with
  * zero first row and column (top = left = 0) and the planner's defaults.
  *
- * No context is used: all scratch (step bits, carry rows, column-table
- * offsets, ticket and error words) lives in one fixed 32 MiB __device__
+ * No context is used: all scratch (step bits, carry rows, prefix-sum
+ * partials, ticket and error words) lives in one fixed 32 MiB __device__
  * array inside this library, which every GPU that loads the library keeps
  * until the process exits.  The call allocates nothing (no cudaMalloc,
  * cudaFree or allocating library routine).
@@ -174,9 +174,11 @@ int paco_lcs_boundaries_host(paco_ctx *ctx, const uint8_t *a, int64_t n,
  * All calls on a device share the one array and keep the previous call's
  * contents (each call clears what must start at zero): calls that overlap on
  * the GPU race, so serialise them.  Returns PACO_EINVAL for bad arguments or
- * when the table needs more than the 32 MiB of scratch (roughly: more than
- * about 6 million columns in the shorter string), PACO_EDEVICE for a CUDA
- * error. */
+ * when the table needs more than the 32 MiB of scratch, PACO_EDEVICE for a
+ * CUDA error.  The scratch is mostly the strips' carry rows, (strips + 1) x
+ * S / 4 bytes with S the shorter side and about one strip per 992 rows of
+ * the longer side (fewer, taller strips once they would not all be
+ * resident): square tables fit up to about 360,000 per side. */
 int paco_lcs_boundaries_static(const uint8_t *a, int64_t n, const uint8_t *b, int64_t m,
                                int32_t *d_bottom_row, int32_t *d_right_col, int32_t *d_len,
                                void *stream);

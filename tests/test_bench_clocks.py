@@ -1,0 +1,88 @@
+"""Host logic of bench.py's clock record, on CPU with a stand-in nvidia-smi.
+
+The stand-in prints one CSV line per period in the query's column order
+(index, clocks.sm, clocks.max.sm, power.draw, reasons.active, hw_slowdown,
+hw_thermal_slowdown, sw_thermal_slowdown, sw_power_cap); the SM clock counts
+up by one per line, so a test can tell which lines were kept.
+"""
+import os
+import stat
+import sys
+import time
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+
+def _fake_smi(tmp_path, reason_from=None):
+    script = tmp_path / "nvidia-smi"
+    reason = "-1" if reason_from is None else str(reason_from)
+    script.write_text(f"""#!{sys.executable}
+import sys, time
+period = 0.05
+for a in sys.argv:
+    if a.isdigit():
+        period = int(a) / 1000.0
+k = 0
+while True:
+    slow = "Active" if {reason} >= 0 and k >= {reason} else "Not Active"
+    print(f"0, {{1000 + k}}, 2070, 500.0, 0x0, Not Active, {{slow}}, Not Active, Not Active", flush=True)
+    k += 1
+    time.sleep(period)
+""")
+    script.chmod(script.stat().st_mode | stat.S_IEXEC)
+    return str(tmp_path)
+
+
+@pytest.fixture
+def bench_mod(monkeypatch):
+    import importlib
+    import bench
+    return importlib.reload(bench)
+
+
+def test_samples_only_from_the_timed_region(tmp_path, monkeypatch, bench_mod):
+    monkeypatch.setenv("PATH", _fake_smi(tmp_path) + os.pathsep + os.environ["PATH"])
+    with bench_mod.ClockSampler(0) as clocks:
+        first_line_seen = len(clocks.lines) >= 1   # the region starts after the first sample
+        time.sleep(0.4)
+    s = clocks.summary()
+    assert first_line_seen
+    assert s["in_region"] and s["samples"] >= 4
+    assert s["sm_max_mhz"] == 2070.0 and s["reasons"] == []
+    # lines stamped before the region began are not in the median: the first
+    # line (1000 MHz) came before the region, so the median is above it
+    assert s["sm_mhz"] > 1000.0
+    assert 350.0 <= s["region_ms"] <= 1000.0
+
+
+def test_throttle_reason_seen_inside_the_region(tmp_path, monkeypatch, bench_mod):
+    monkeypatch.setenv("PATH", _fake_smi(tmp_path, reason_from=3) + os.pathsep + os.environ["PATH"])
+    with bench_mod.ClockSampler(0) as clocks:
+        time.sleep(0.5)
+    s = clocks.summary()
+    assert "hw_thermal_slowdown" in s["reasons"]
+
+
+def test_short_region_falls_back_to_the_next_sample(tmp_path, monkeypatch, bench_mod):
+    monkeypatch.setenv("PATH", _fake_smi(tmp_path) + os.pathsep + os.environ["PATH"])
+    monkeypatch.setattr(bench_mod.ClockSampler, "PERIOD_MS", 300)
+    with bench_mod.ClockSampler(0) as clocks:
+        pass
+    # stop the stand-in's reader from adding lines after the region
+    s = clocks.summary()
+    assert s is not None and s["samples"] >= 1
+
+
+def test_no_nvidia_smi_gives_no_record(tmp_path, monkeypatch, bench_mod):
+    monkeypatch.setenv("PATH", str(tmp_path))   # an empty directory: no nvidia-smi at all
+    with bench_mod.ClockSampler(0) as clocks:
+        pass
+    assert clocks.summary() is None
+
+
+def test_default_steps_per_workload(bench_mod):
+    assert bench_mod.DEFAULT_STEPS["mutated"] * 2.4e-3 >= 0.3   # about half a second of pair steps
+    assert all(v >= 10 for v in bench_mod.DEFAULT_STEPS.values())
