@@ -1,4 +1,6 @@
-"""Host logic of bench.py's clock record, on CPU with a stand-in nvidia-smi.
+"""Host logic of bench.py on CPU: the clock record (with a stand-in
+nvidia-smi) and the per-launch DRAM traffic taken from the committed ncu
+summaries only while the kernel sources are the profiled ones.
 
 The stand-in prints one CSV line per period in the query's column order
 (index, clocks.sm, clocks.max.sm, power.draw, reasons.active, hw_slowdown,
@@ -86,3 +88,37 @@ def test_no_nvidia_smi_gives_no_record(tmp_path, monkeypatch, bench_mod):
 def test_default_steps_per_workload(bench_mod):
     assert bench_mod.DEFAULT_STEPS["mutated"] * 2.4e-3 >= 0.3   # about half a second of pair steps
     assert all(v >= 10 for v in bench_mod.DEFAULT_STEPS.values())
+
+
+def test_profiled_traffic_only_while_the_kernel_source_is_unchanged(tmp_path, monkeypatch, bench_mod):
+    """roofline.traffic comes from a committed ncu summary only while the
+    kernel's sources hash to the ones that were profiled; any edit of them
+    turns it into null."""
+    import shutil
+    root = tmp_path / "tree"
+    (root / "profiles").mkdir(parents=True)
+    csrc = root / "paper_2011_01441_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    for f in ("pair_kernels.cu", "bp_device.cuh"):
+        shutil.copy(os.path.join(ROOT, "paper_2011_01441_gb300", "csrc", f), csrc / f)
+    shutil.copy(os.path.join(ROOT, "profiles", "k_pair_bp_pair131072_launches.md"), root / "profiles")
+    monkeypatch.setattr(bench_mod, "ROOT", str(root))
+    srcs = ["pair_kernels.cu", "bp_device.cuh"]
+    committed = bench_mod._profiled_traffic("k_pair_bp_pair131072_launches.md", srcs)
+    assert isinstance(committed, int) and committed > 0
+    with open(csrc / "bp_device.cuh", "a") as f:
+        f.write("\n// an edit after the capture\n")
+    assert bench_mod._profiled_traffic("k_pair_bp_pair131072_launches.md", srcs) is None
+    assert bench_mod._profiled_traffic("no_such_summary.md", srcs) is None
+
+
+def test_every_committed_summary_matches_its_kernel_source(bench_mod):
+    """Each ncu summary that carries a traffic figure was taken on the kernel
+    source as committed (so the bench reports it, not null)."""
+    cases = {"k_pair_bp_pair131072_launches.md": ["pair_kernels.cu", "bp_device.cuh"],
+             "k_batch_batch4096_full.md": ["batch.cu", "bp_device.cuh"],
+             "k_affine_batch4096_full.md": ["affine.cu", "bp_device.cuh"],
+             "k_affine_pair131072_launches.md": ["affine.cu", "bp_device.cuh"],
+             "k_lws_n131072_full.md": ["lws.cu", "bp_device.cuh"]}
+    for prof, srcs in cases.items():
+        assert bench_mod._profiled_traffic(prof, srcs) is not None, prof
