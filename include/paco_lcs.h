@@ -92,9 +92,10 @@ int paco_ctx_set_option(paco_ctx *ctx, int option, int64_t value);
 int paco_ctx_get_option(paco_ctx *ctx, int option, int64_t *value);
 
 enum paco_option {
-    PACO_OPT_ENGINE = 1,        /* 0 = auto, 1 = bit-parallel, 2 = cell-wise   */
+    PACO_OPT_ENGINE = 1,        /* 0 = auto, 1 = bit-parallel (the only engine) */
     PACO_OPT_CHUNK = 2,         /* columns per lane hand-off: 2, 4 or 8 (0 = planner) */
-    PACO_OPT_WARPS = 3,         /* warps per CTA strip (0 = planner)           */
+    PACO_OPT_WARPS = 3,         /* compute warps per CTA strip, 0..7 (0 = planner); more
+                                   than fit in shared memory are clamped */
     PACO_OPT_WAIT_LIMIT_NS = 4, /* bounded-wait limit per wait, ns (default 2e9) */
     PACO_OPT_ORIENT = 5,        /* 0 = planner, 1 = bits along a, 2 = along b  */
     PACO_OPT_SCHEDULE = 6,      /* 0 = PACO balanced strips, 1 = uniform strips */
@@ -166,11 +167,16 @@ int paco_lcs_boundaries_host(paco_ctx *ctx, const uint8_t *a, int64_t n,
  * cudaFree or allocating library routine).
  *   a, b        : device uint8[n], uint8[m]
  *   d_bottom_row: device int32[m+1] or NULL;  d_right_col: int32[n+1] or NULL
- *   d_len       : device int32[1] or NULL; receives L, or a negative
- *                 paco_status if a device wait timed out
- * Stream ordered (stream = cudaStream_t or NULL).  The first call on a
- * device, with that device current, resolves the array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   d_len       : device int32[1], required (NULL is PACO_EINVAL); receives
+ *                 L, or a negative paco_status (PACO_ETIMEOUT) when a device
+ *                 wait timed out, in which case the boundaries are void
+ * Every buffer must be on the CURRENT device: the call takes the scratch of
+ * the device that is current (cudaGetDevice) and launches on `stream`, which
+ * must belong to that device.  Stream ordered (stream = cudaStream_t or
+ * NULL).  Each call looks up the array's device address on the current
+ * device (cudaGetSymbolAddress, no allocation); the first lookup on a device
+ * loads the library's device code there, so make the first call on each
+ * device before any stream capture.
  * All calls on a device share the one array and keep the previous call's
  * contents (each call clears what must start at zero): calls that overlap on
  * the GPU race, so serialise them.  Returns PACO_EINVAL for bad arguments or
@@ -247,12 +253,16 @@ int paco_lcs_submit_many(paco_ctx *ctx, const uint8_t *a_cat, const int64_t *a_o
 int paco_lcs_poll_many(paco_ctx *ctx, const uint64_t *tickets, int64_t count, int32_t *len,
                        int32_t *status, int64_t *n_done);
 
-/* Serving statistics since the context was created (host monotonic clock,
- * seconds): completed requests, cells, queue and in-flight counts. */
+/* Serving statistics since the context was created: requests submitted and
+ * completed, cells computed, queue and in-flight counts, micro-batches
+ * launched, device bytes held and the budget, and the engine thread's host
+ * time (ns) spent preparing and launching micro-batches and collecting
+ * their results. */
 typedef struct paco_serve_stats {
     uint64_t submitted, completed, cells_done;
     uint64_t queued_now, inflight_now, batches_launched;
     uint64_t bytes_in_use, bytes_budget;
+    uint64_t host_launch_ns, host_complete_ns;
 } paco_serve_stats;
 int paco_serve_get_stats(paco_ctx *ctx, paco_serve_stats *out);
 

@@ -81,7 +81,7 @@ class PacoLwsWeight(ctypes.Structure):
 class PacoServeStats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_uint64) for k in
                 ("submitted", "completed", "cells_done", "queued_now", "inflight_now",
-                 "batches_launched", "bytes_in_use", "bytes_budget")]
+                 "batches_launched", "bytes_in_use", "bytes_budget", "host_launch_ns", "host_complete_ns")]
 
 
 def load():
@@ -242,21 +242,44 @@ def paco_lcs_boundaries(ctx: Context, a, b, top=None, left=None, bottom_row=None
 
 
 def paco_lcs_boundaries_static(a, b, bottom_row=None, right_col=None, length=None, stream=None,
-                               want_rows=True, want_cols=True):
+                               want_rows=True, want_cols=True, checked=False):
     """The allocation-free variant (see include/paco_lcs.h): zero boundaries,
     scratch in the library's fixed device array.  Outputs are allocated here
-    by torch only when not given."""
+    by torch only when not given; a caller that cannot allocate passes all
+    three.  The call runs with a's device made current; every tensor must be
+    on that device.
+
+    A device wait that timed out shows up as a NEGATIVE value in `length` (a
+    paco_status), not as an exception, because the call is stream ordered.
+    With checked=True the stream is synchronised and a negative length
+    raises PacoError."""
     import torch
     a, b = _u8(a, "a"), _u8(b, "b")
     n, m = a.numel(), b.numel()
-    if want_rows and bottom_row is None:
-        bottom_row = torch.empty(m + 1, dtype=torch.int32, device=a.device)
-    if want_cols and right_col is None:
-        right_col = torch.empty(n + 1, dtype=torch.int32, device=a.device)
-    if length is None:
-        length = torch.empty(1, dtype=torch.int32, device=a.device)
-    _check(load().paco_lcs_boundaries_static(_ptr(a), n, _ptr(b), m, _ptr(bottom_row), _ptr(right_col),
-                                             _ptr(length), _stream(stream)))
+    dev = a.device
+    with torch.cuda.device(dev):
+        if want_rows and bottom_row is None:
+            bottom_row = torch.empty(m + 1, dtype=torch.int32, device=dev)
+        if want_cols and right_col is None:
+            right_col = torch.empty(n + 1, dtype=torch.int32, device=dev)
+        if length is None:
+            length = torch.empty(1, dtype=torch.int32, device=dev)
+        for t, k, name in ((b, m, "b"), (bottom_row, m + 1, "bottom_row"), (right_col, n + 1, "right_col"),
+                           (length, 1, "length")):
+            if t is None:
+                continue
+            if t.device != dev:
+                raise ValueError(f"{name} is on {t.device}, a is on {dev}: every buffer must share one device")
+            if t is not b and (t.dtype != torch.int32 or t.numel() < k or not t.is_contiguous()):
+                raise ValueError(f"{name} must be a contiguous int32 tensor of at least {k} values")
+        st = torch.cuda.current_stream(dev) if stream is None else stream
+        _check(load().paco_lcs_boundaries_static(_ptr(a), n, _ptr(b), m, _ptr(bottom_row), _ptr(right_col),
+                                                 _ptr(length), ctypes.c_void_p(st.cuda_stream)))
+        if checked:
+            st.synchronize()
+            v = int(length[0].item())
+            if v < 0:
+                raise PacoError(v, "device-side failure in paco_lcs_boundaries_static")
     return length, bottom_row, right_col
 
 

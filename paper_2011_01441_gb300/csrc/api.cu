@@ -126,7 +126,7 @@ void paco_ctx_destroy(paco_ctx *ctx) {
     ctx->affine = nullptr;
     lws_state_free(ctx->lws);
     ctx->lws = nullptr;
-    for (DevBuf *b : {&ctx->small, &ctx->hbuf, &ctx->lbits, &ctx->rbits, &ctx->rows, &ctx->sums,
+    for (DevBuf *b : {&ctx->small, &ctx->hbuf,
                       &ctx->h_a, &ctx->h_b, &ctx->h_top, &ctx->h_left, &ctx->h_row, &ctx->h_col,
                       &ctx->h_len}) {
         if (b->ptr) cudaFree(b->ptr);
@@ -142,7 +142,7 @@ int paco_ctx_set_option(paco_ctx *ctx, int option, int64_t value) {
     if (!ctx) return PACO_EINVAL;
     switch (option) {
         case PACO_OPT_ENGINE:
-            if (value < 0 || value > 2) return PACO_EINVAL;
+            if (value < 0 || value > 1) return PACO_EINVAL;
             ctx->opt_engine = (int)value;
             return PACO_OK;
         case PACO_OPT_CHUNK:
@@ -150,8 +150,8 @@ int paco_ctx_set_option(paco_ctx *ctx, int option, int64_t value) {
                 return PACO_EINVAL;
             ctx->opt_chunk = (int)value;
             return PACO_OK;
-        case PACO_OPT_WARPS:
-            if (value < 0 || value > pair_max_warps(1)) return PACO_EINVAL;
+        case PACO_OPT_WARPS:  // the planner clamps to what fits in shared memory
+            if (value < 0 || value > 7) return PACO_EINVAL;
             ctx->opt_warps = (int)value;
             return PACO_OK;
         case PACO_OPT_WAIT_LIMIT_NS:

@@ -128,6 +128,22 @@ static __device__ __forceinline__ void column31v(uint32_t &V, uint32_t &sr, uint
         : "r"(M));
 }
 
+// Plain (weak) 64-bit shared-memory load and predicated store of a tagged
+// word (tag in the high half, data in the low half).  One aligned 64-bit
+// access is a single transaction, so a reader sees either the old word or the
+// new one, and the tag tells which: the steady state needs no strong access
+// (a volatile or relaxed one costs the warp a few hundred cycles in this
+// loop); only the wait loops that run when a tag is stale read strongly.
+static __device__ __forceinline__ uint64_t lds_u64(uint32_t addr) {
+    uint64_t v;
+    asm volatile("ld.shared.u64 %0, [%1];" : "=l"(v) : "r"(addr));
+    return v;
+}
+static __device__ __forceinline__ void sts_u64_if(bool p, uint32_t addr, uint64_t v) {
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %0, 0;\n\t@q st.shared.u64 [%1], %2;\n\t}"
+                 ::"r"((uint32_t)p), "r"(addr), "l"(v));
+}
+
 static __device__ __forceinline__ int ld_acquire_shared(uint32_t addr) {
     int v;
     asm volatile("ld.acquire.cta.shared.s32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
@@ -135,6 +151,11 @@ static __device__ __forceinline__ int ld_acquire_shared(uint32_t addr) {
 }
 static __device__ __forceinline__ void st_release_shared(uint32_t addr, int v) {
     asm volatile("st.release.cta.shared.s32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+// The same, predicated (no branch around a one-lane store).
+static __device__ __forceinline__ void st_release_shared_if(bool p, uint32_t addr, int v) {
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %0, 0;\n\t@q st.release.cta.shared.s32 [%1], %2;\n\t}"
+                 ::"r"((uint32_t)p), "r"(addr), "r"(v) : "memory");
 }
 }  // namespace dev
 }  // namespace paco

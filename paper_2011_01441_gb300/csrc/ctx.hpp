@@ -23,10 +23,9 @@ struct TileState;
 struct AffineState;
 struct LwsState;
 
-// A pair plan plus its strip offsets resident on the device.
+// A pair plan (the strips' rows are computed in the kernel from its counts).
 struct CachedPairPlan {
     PairPlan plan;
-    DevBuf d_row0;
 };
 }  // namespace paco
 
@@ -35,10 +34,11 @@ struct paco_ctx {
     int sms = 0;
     size_t budget = 0;
     std::mutex mu;
-    // small: [0] error word, [1] ticket, sink from byte 1024
+    // small: [0] error word, [1] batch ticket, [4..5] the pair kernel's strip ticket and exit
+    // count (zero between launches), sink from byte 1024
     DevBuf small;
-    // single-pair scratch
-    DevBuf hbuf, lbits, rbits, rows, sums;
+    // single-pair scratch: the strips' tagged carry rows
+    DevBuf hbuf;
     // staging for the host-buffer entry point
     DevBuf h_a, h_b, h_top, h_left, h_row, h_col, h_len;
     uint32_t epoch = 0;
@@ -65,6 +65,7 @@ struct paco_ctx {
 
     int *err_ptr() { return (int *)small.ptr; }
     int *ticket_ptr() { return (int *)small.ptr + 1; }
+    int *pair_ctl_ptr() { return (int *)small.ptr + 4; }
     uint32_t *sink_ptr() { return (uint32_t *)((char *)small.ptr + 1024); }
 };
 

@@ -1,4 +1,5 @@
-// Single-pair LCS kernels for sm_103a.
+// Single-pair LCS kernel for sm_103a: the whole path of one table in one
+// launch.
 //
 // The table of Eq. (1) (Tang & Gao, Sec. "PACO LCS") is computed on its
 // unit steps: in an LCS table neighbouring entries differ by 0 or 1, so a
@@ -15,14 +16,27 @@
 // stays set, so the carry flag of the 32-bit add is the carry out); a warp
 // holds 32 lanes x 31 rows, and each lane hands the carry bits of a chunk of
 // C columns to the lane below through __shfl_up_sync.  Warps of one CTA
-// strip chain through a shared-memory ring, and CTA strips chain through
+// strip chain through shared-memory rings, and CTA strips chain through
 // global memory with epoch-tagged words.  One extra warp per CTA produces:
-// it turns the column string into match-table offsets and polls the strip
-// above for its carry words, both into shared rings, so the compute warps
-// never wait on global memory.  The PACO execution phase (regions run in
-// anti-diagonal order, each waiting only on its neighbours, no global
-// barrier) is this pipeline: lane g of strip s works on chunk q at step
-// q + 2g.
+// it turns the column string into match-table offsets and delivers the
+// strip's input carry words (the strip above's output, or the top boundary's
+// steps for the first strip), so the compute warps never wait on global
+// memory.  The PACO execution phase (regions run in anti-diagonal order,
+// each waiting only on its neighbours, no global barrier) is this pipeline:
+// lane g of strip s works on chunk q at step q + 3g.
+//
+// Everything around the table runs in the same launch:
+// - the input boundaries are read as values: each lane turns its rows of the
+//   left boundary into its first column's steps, and the first strip's
+//   producer turns the top boundary into carry words (both checked to be
+//   unit-step boundaries);
+// - the right column needs no scan: a warp's first row r0 has
+//   H[r0][S] = H[r0][0] + (horizontal steps along row r0), the set bits of the
+//   carry words the warp consumed, so each warp writes its own rows of the
+//   right column from that base and its lanes' last-column steps;
+// - the last strip's producer expands the bottom row's carry words into
+//   values as the last warp hands them over, and writes L;
+// - the last CTA to leave resets the strip ticket for the next launch.
 #include "paco_internal.hpp"
 #include "bp_device.cuh"
 
@@ -34,17 +48,21 @@ namespace {
 
 using namespace dev;
 
-// Lane skew in chunks: with one word per lane, lane k works on chunk t - 2k
+// Lane skew in chunks: with one word per lane, lane k works on chunk t - 3k
 // at step t; with two words (the lower word one chunk behind the upper, fed
-// by its carries in registers) lane k's upper word works on chunk t - 3k.
+// by its carries in registers) lane k's upper word works on chunk t - 4k.
 // Either way the carry word a lane receives from the lane above (one
-// __shfl_up_sync after each step's columns) was sent two steps before it is
-// needed.
-template <int WPL> __host__ __device__ constexpr int lane_skew() { return WPL == 1 ? 2 : 3; }
+// __shfl_up_sync after each step's columns) was sent three steps before it
+// is needed, which keeps the shuffle's latency off the column chain.
+template <int WPL> __host__ __device__ constexpr int lane_skew() { return WPL == 1 ? 3 : 4; }
 // Chunks the last word of lane 31 trails the first word of lane 0.
 template <int WPL> __host__ __device__ constexpr int lane_lag() { return lane_skew<WPL>() * 31 + (WPL - 1); }
-// Warp 0's input carry words pass through a shared ring of kSrcSlots words.
+// Warp 0's input carry words pass through a ring of tagged 64-bit words
+// (the word index + 1 in the high half), so reading one needs no fence.
 constexpr int kSrcSlots = 64;
+// The compute warps check the column ring's fill level (an acquire load) and
+// publish their progress (a release store) once per this many 32-column words.
+constexpr int kCheckEvery = 4;
 // A match table holds one 32-lane row per symbol and one all-zero row after
 // them: columns outside [0, S) (before the first column while the lanes'
 // pipeline fills, past the last one while it drains) read that row, so an
@@ -55,13 +73,13 @@ constexpr uint32_t kZeroRow = (uint32_t)kMaxSigma * 128u;
 // Column-word lag of the oldest word a warp still reads behind the word its
 // lane 0 is on (the lower word reuses the upper word's offsets).
 __host__ __device__ constexpr int col_lag_words(int C, int WPL) {
-    return ((WPL == 1 ? 2 : 3) * 31 * C + 31) / 32 + 1;
+    return ((WPL == 1 ? 3 : 4) * 31 * C + (WPL - 1) * C + 31) / 32 + 1;
 }
 // Column-offset ring slots (a power of two) for C, W compute warps and WPL
-// words per lane: the lag of the last warp behind the first, the in-warp lag
-// and some lookahead.
+// words per lane: the lag of the last warp behind the first, the in-warp lag,
+// the look-ahead of one check period and the staleness of the progress words.
 __host__ __device__ constexpr int col_slots(int C, int W, int WPL) {
-    const int need = col_lag_words(C, WPL) + 4 + (W - 1) * (col_lag_words(C, WPL) + 2) + 8;
+    const int need = col_lag_words(C, WPL) + 2 * kCheckEvery + 4 + (W - 1) * (col_lag_words(C, WPL) + 2) + 8;
     int r = 32;
     while (r < need) r <<= 1;
     return r;
@@ -69,8 +87,10 @@ __host__ __device__ constexpr int col_slots(int C, int W, int WPL) {
 
 // Shared-memory layout of one CTA: W x WPL match tables, the column-offset
 // ring (slots + two mirror slots, so a lane's window of the next 32 + 2C
-// columns never wraps), the input ring of warp 0, the rings between
-// consecutive warps, counters.
+// columns never wraps), the tagged input ring of warp 0, the tagged rings
+// after each warp (the last one carries the bottom row to the producer in the
+// last strip), and the counters: the producer's column count, then one
+// progress word per compute warp and the producer's bottom-row count.
 struct PairSmem {
     uint32_t tables, colring, srcring, rings, ctrl, bytes;
 };
@@ -79,25 +99,22 @@ __host__ __device__ inline PairSmem pair_smem_layout(int W, int C, int WPL) {
     L.tables = 0;
     L.colring = (uint32_t)(W * WPL * kPairTableBytes);
     L.srcring = L.colring + (uint32_t)(col_slots(C, W, WPL) + 2) * 128u;
-    L.rings = L.srcring + (uint32_t)kSrcSlots * 4u;
+    L.rings = L.srcring + (uint32_t)kSrcSlots * 8u;
     L.ctrl = L.rings + (uint32_t)(W * kRing * 8);
     L.bytes = L.ctrl + (uint32_t)(2 + W) * 4u + 16u;
     return L;
 }
 
-// Compute warps wait here (uniformly: every lane reads the same words) when
-// the producer or the warp above is behind.  Bounded: false on a timeout or
-// a raised error.
-static __device__ __noinline__ bool wait_inputs(uint32_t prod_cols, uint32_t prod_src, int need_c,
-                                                int need_s, const uint64_t *ring_word, uint32_t tag,
-                                                int *err, long long limit) {
+static __device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Compute warps wait here (uniformly: every lane reads the same word) for the
+// column ring.  Bounded: false on a timeout or a raised error.
+static __device__ __noinline__ bool wait_cols(uint32_t prod_cols, int need, int *err, long long limit) {
     const uint64_t t0 = global_ns();
     bool ok = true;
-    for (;;) {
-        bool ready = ld_acquire_shared(prod_cols) >= need_c;
-        if (need_s > 0) ready = ready && ld_acquire_shared(prod_src) >= need_s;
-        if (ring_word) ready = ready && (uint32_t)(*reinterpret_cast<const volatile uint64_t *>(ring_word) >> 32) == tag;
-        if (ready) break;
+    while (ld_acquire_shared(prod_cols) < need) {
         if (ld_relaxed_i32(err) != 0) { ok = false; break; }
         if ((long long)(global_ns() - t0) > limit) {
             raise_error(err, kEtimeout);
@@ -108,11 +125,64 @@ static __device__ __noinline__ bool wait_inputs(uint32_t prod_cols, uint32_t pro
     return __all_sync(kFull, ok);
 }
 
+// ... and for a tagged input word (bounded like every wait): returns the
+// word; its tag is still stale only after a timeout or a raised error.
+static __device__ __noinline__ uint64_t wait_tagged(const uint64_t *slot, uint32_t tag, int *err, long long limit) {
+    const uint64_t t0 = global_ns();
+    uint64_t v;
+    for (;;) {
+        v = *reinterpret_cast<const volatile uint64_t *>(slot);
+        if ((uint32_t)(v >> 32) == tag) break;
+        if (ld_relaxed_i32(err) != 0) break;
+        if ((long long)(global_ns() - t0) > limit) {
+            raise_error(err, kEtimeout);
+            break;
+        }
+    }
+    return v;
+}
+
 // The match words of one chunk: the lane's row bits for each column's symbol.
 template <int C>
 static __device__ __forceinline__ void match_words(uint32_t pm_lane, const uint32_t (&o)[C], uint32_t (&M)[C]) {
 #pragma unroll
     for (int jj = 0; jj < C; ++jj) M[jj] = lds_u32(pm_lane + o[jj]);
+}
+
+// Column offsets of one chunk from the ring.
+template <int C>
+static __device__ __forceinline__ void offs_at(uint32_t addr, uint32_t (&o)[C]) {
+    if constexpr (C == 2) {
+        uint32_t x, y;
+        asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(x), "=r"(y) : "r"(addr));
+        o[0] = x;
+        o[1] = y;
+    } else {
+#pragma unroll
+        for (int k = 0; k < C / 4; ++k) {
+            uint32_t x, y, z, v;
+            asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                         : "=r"(x), "=r"(y), "=r"(z), "=r"(v) : "r"(addr + 16 * k));
+            o[4 * k] = x;
+            o[4 * k + 1] = y;
+            o[4 * k + 2] = z;
+            o[4 * k + 3] = v;
+        }
+    }
+}
+
+// Rows [row0, row1) of strip s: the PACO p-way first cut in lane granules
+// (parts differ by at most one granule), or uniform strips.
+static __device__ __forceinline__ void strip_rows(const PairArgs &P, int s, int64_t rows_lane, int64_t &row0,
+                                                  int64_t &row1) {
+    if (P.uniform_rows > 0) {
+        row0 = min(P.L, (int64_t)s * P.uniform_rows);
+        row1 = min(P.L, row0 + P.uniform_rows);
+    } else {
+        const int64_t q = P.granules / P.nstrips, r = P.granules % P.nstrips;
+        row0 = min(P.L, rows_lane * ((int64_t)s * q + min((int64_t)s, r)));
+        row1 = min(P.L, rows_lane * ((int64_t)(s + 1) * q + min((int64_t)(s + 1), r)));
+    }
 }
 
 template <int C, int WPL>
@@ -126,20 +196,24 @@ __global__ void __launch_bounds__(256, 1) k_pair_bp(const PairArgs P) {
     const int lane = threadIdx.x & 31;
     const PairSmem lay = pair_smem_layout(W, C, WPL);
     const int R = col_slots(C, W, WPL);
-    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
+    const uint32_t sbase = smem_addr(smem);
     const uint32_t col_ring = sbase + lay.colring;
-    const uint32_t src_ring = sbase + lay.srcring;
-    const uint32_t prod_cols = sbase + lay.ctrl, prod_src = prod_cols + 4, cons0 = prod_cols + 8;
+    const uint32_t prod_cols = sbase + lay.ctrl;
+    const uint32_t cons_s = prod_cols + 4;  // progress word v (v = 0..W) at cons_s + 4 v
+    volatile int *cons = reinterpret_cast<volatile int *>(smem + lay.ctrl + 4);
+    uint64_t *srcq = reinterpret_cast<uint64_t *>(smem + lay.srcring);
     uint64_t *rings = reinterpret_cast<uint64_t *>(smem + lay.rings);
-    uint64_t *ring_out = rings + (size_t)w * kRing;                       // read by warp w+1
-    const uint32_t ring_out_s = (uint32_t)__cvta_generic_to_shared(ring_out);
-    const uint64_t *ring_in = rings + (size_t)(w > 0 ? w - 1 : 0) * kRing;  // written by warp w-1
-    volatile int *cons = reinterpret_cast<volatile int *>(smem + lay.ctrl + 8);
+    uint64_t *ring_out = rings + (size_t)(w < W ? w : W - 1) * kRing;        // read by warp w+1 / the producer
+    const uint32_t ring_out_s = smem_addr(ring_out);
+    const uint64_t *ring_in = rings + (size_t)(w > 0 && w < W ? w - 1 : 0) * kRing;  // written by warp w-1
+    // where this warp's input carry words arrive: warp 0's from the producer
+    const uint32_t in_s = w == 0 ? smem_addr(srcq) : smem_addr(ring_in);
+    const uint32_t in_mask = w == 0 ? (uint32_t)(kSrcSlots - 1) : (uint32_t)(kRing - 1);
     // table of word x of this warp (x = 0 upper, 1 lower)
     uint32_t *pm0 = reinterpret_cast<uint32_t *>(smem + (size_t)(w < W ? w * WPL : 0) * kPairTableBytes);
     uint32_t *pm1 = pm0 + (WPL == 2 ? kPairTableBytes / 4 : 0);
-    const uint32_t pm_lane0 = (uint32_t)__cvta_generic_to_shared(pm0 + lane);
-    const uint32_t pm_lane1 = (uint32_t)__cvta_generic_to_shared(pm1 + lane);
+    const uint32_t pm_lane0 = smem_addr(pm0 + lane);
+    const uint32_t pm_lane1 = smem_addr(pm1 + lane);
 
     if (w < W)
         for (int c = 0; c < (kMaxSigma + 1) * WPL; ++c) pm0[c * 32 + lane] = 0u;
@@ -153,90 +227,154 @@ __global__ void __launch_bounds__(256, 1) k_pair_bp(const PairArgs P) {
     constexpr int kFlushStep = (kLag - 1) % K;      // step at which lane 31 completes a word
     constexpr int kLagW = col_lag_words(C, WPL);
     constexpr int kRowsLane = kLaneRows * WPL;
-    const int64_t nwords = P.nwords;
+    const int nwords = P.nwords;
     // words lane 0 runs over: the real ones, then zero-row words until the
     // last lane has finished the last real word
-    const int64_t nouter = (nwords * K + kLag + K - 1) / K;
-    const int64_t nvwords = nouter + 2;             // words the producer writes (with the prefetch)
+    const int nouter = (nwords * K + kLag + K - 1) / K;
+    const int nvwords = nouter + 2;                 // words the producer writes (with the prefetch)
+    const int32_t *top = P.top, *left = P.left;
 
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) {
-            int s = atomicAdd(P.ticket, 1);
+            int s = atomicAdd(P.ctl, 1);
             if (ld_relaxed_i32(P.err) != 0) s = P.nstrips;
             s_strip = s;
             st_release_shared(prod_cols, 0);
-            st_release_shared(prod_src, 0);
         }
-        if (w < W) {
-            for (int i = lane; i < kRing; i += 32) ring_out[i] = 0ull;
-            if (lane == 0) cons[w] = 0;
+        if (threadIdx.x <= W) cons[threadIdx.x] = 0;
+        for (int i = threadIdx.x; i < kSrcSlots + W * kRing; i += blockDim.x) {
+            if (i < kSrcSlots) srcq[i] = 0ull;
+            else rings[i - kSrcSlots] = 0ull;
         }
         __syncthreads();
         const int s = s_strip;
         if (s >= P.nstrips) break;
-        const uint64_t *src_row = P.hbuf + (size_t)s * P.hstride;
-        uint64_t *dst_row = P.hbuf + (size_t)(s + 1) * P.hstride;
-        const uint32_t want = (s == P.stall_strip) ? (P.epoch ^ 0x80000000u) : P.epoch;
+        const bool last_strip = s == P.nstrips - 1;
+        int64_t row0, row1;
+        strip_rows(P, s, kRowsLane, row0, row1);
 
         if (w == W) {
             // ---------------- producer warp ----------------
             // Column offsets (symbol x 128 bytes) from b into the ring, as far
-            // ahead as the slowest compute warp allows; the strip's input
-            // carry words, polled in global memory 32 at a time, into the
-            // input ring of warp 0.
-            int64_t qc = 0, qs = 0;
+            // ahead as the slowest compute warp allows; warp 0's input carry
+            // words (the strip above's output polled in global memory, or the
+            // top boundary's steps) into the tagged input ring; in the last
+            // strip, the bottom row's carry words into values.
+            int qc = 0, qs = 0, qb = 0;
+            int32_t run = 0;  // bottom row: H[L][j] of the last column expanded
+            const uint64_t *src_row = P.hbuf + (size_t)s * P.hstride;
+            const uint32_t want = (s == P.stall_strip) ? (P.epoch ^ 0x80000000u) : P.epoch;
+            uint32_t *ring = reinterpret_cast<uint32_t *>(smem + lay.colring);
+            const uint64_t *bq = rings + (size_t)(W - 1) * kRing;
+            // the words before column 0 (read while the lanes' pipeline fills): zero rows
+            for (int j = 1; j <= kLagW + 1; ++j) ring[(uint32_t)((R - j) & (R - 1)) * 32 + lane] = kZeroRow;
+            __syncwarp();
+            if (s == 0 && lane == 0) {  // H[0][0] is both boundaries' first value
+                const int32_t t0 = top ? top[0] : 0, l0 = left ? left[0] : 0;
+                if (t0 != l0) raise_error(P.err, kEinval);
+            }
+            if (last_strip) {
+                run = left ? left[P.L] : 0;
+                if (lane == 0 && P.bottom) P.bottom[0] = run;
+            }
             int idle = 0;
             uint64_t t_idle = global_ns();
-            {   // the words before column 0 (read while the lanes' pipeline fills): zero rows
-                uint32_t *ring = reinterpret_cast<uint32_t *>(smem + lay.colring);
-                for (int j = 1; j <= kLagW + 1; ++j) ring[(uint32_t)((R - j) & (R - 1)) * 32 + lane] = kZeroRow;
-                __syncwarp();
-            }
-            while (qc < nvwords || qs < nwords) {
+            bool ok = true;
+            while (qc < nvwords || qs < nwords || (last_strip && qb < nwords)) {
                 bool progress = false;
                 int minc = cons[0];
                 for (int v = 1; v < W; ++v) minc = min(minc, cons[v]);
-                const int64_t lim_c = min(nvwords, (int64_t)minc - 1 - kLagW + R);
+                const int lim_c = min(nvwords, minc - 1 - kLagW + R);
                 if (qc < lim_c) {
-                    const int64_t qe = min(lim_c, qc + 4);
-                    uint32_t o[4];
+                    const int qe = min(lim_c, qc + 8);
+                    uint32_t o[8];
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const int64_t col = (qc + k) * 32 + lane;
+                    for (int k = 0; k < 8; ++k) {
+                        const int64_t col = (int64_t)(qc + k) * 32 + lane;
                         o[k] = (qc + k < qe && col < P.S) ? (uint32_t)__ldg(P.b + col) * 128u : kZeroRow;
                     }
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
+                    for (int k = 0; k < 8; ++k) {
                         if (qc + k < qe) {
                             const uint32_t slot = (uint32_t)((qc + k) & (R - 1));
-                            uint32_t *ring = reinterpret_cast<uint32_t *>(smem + lay.colring);
                             ring[slot * 32 + lane] = o[k];
                             if (slot < 2) ring[((uint32_t)R + slot) * 32 + lane] = o[k];
                         }
                     }
                     __syncwarp();
-                    if (lane == 0) st_release_shared(prod_cols, (int)qe);
+                    if (lane == 0) st_release_shared(prod_cols, qe);
                     qc = qe;
                     progress = true;
                 }
-                const int64_t lim_s = min(nwords, (int64_t)cons[0] + kSrcSlots - 1);
+                const int lim_s = min(nwords, cons[0] + kSrcSlots - 1);
                 if (qs < lim_s) {
-                    const int64_t q = qs + lane;
+                    if (s > 0) {  // the strip above's output words, as they are published
+                        const int q = qs + lane;
+                        uint64_t v = 0;
+                        bool rd = false;
+                        if (q < lim_s) {
+                            v = ld_relaxed_u64(src_row + q);
+                            rd = (uint32_t)(v >> 32) == want;
+                        }
+                        const uint32_t bal = __ballot_sync(kFull, rd);
+                        const int n = (bal == kFull) ? 32 : (__ffs(~bal) - 1);
+                        if (lane < n) srcq[q & (kSrcSlots - 1)] = ((uint64_t)(uint32_t)(q + 1) << 32) | (uint32_t)v;
+                        if (n > 0) {
+                            qs += n;
+                            progress = true;
+                        }
+                    } else if (top == nullptr) {  // zero top boundary
+                        const int q = qs + lane;
+                        if (q < lim_s) srcq[q & (kSrcSlots - 1)] = (uint64_t)(uint32_t)(q + 1) << 32;
+                        qs = min(lim_s, qs + 32);
+                        progress = true;
+                    } else {  // the top boundary's steps, MSB first, four words per pass
+                        const int qe = min(lim_s, qs + 4);
+                        int32_t v0[4], v1[4];
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            const int64_t col = (int64_t)(qs + k) * 32 + lane;
+                            const bool in = qs + k < qe && col < P.S;
+                            v0[k] = in ? top[col] : 0;
+                            v1[k] = in ? top[col + 1] : 0;
+                        }
+                        bool bad = false;
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            const int32_t d = v1[k] - v0[k];
+                            bad |= (d & ~1) != 0;
+                            const uint32_t word = __brev(__ballot_sync(kFull, (d & 1) != 0));
+                            if (qs + k < qe && lane == k)
+                                srcq[(qs + k) & (kSrcSlots - 1)] = ((uint64_t)(uint32_t)(qs + k + 1) << 32) | word;
+                        }
+                        if (__any_sync(kFull, bad) && lane == 0) raise_error(P.err, kEinval);
+                        qs = qe;
+                        progress = true;
+                    }
+                }
+                if (last_strip && qb < nwords) {  // the bottom row from the last warp's words
+                    const int q = qb + lane;
                     uint64_t v = 0;
                     bool rd = false;
-                    if (q < lim_s) {
-                        v = ld_relaxed_u64(src_row + q);
-                        rd = (uint32_t)(v >> 32) == want;
+                    if (q < nwords) {
+                        v = *reinterpret_cast<const volatile uint64_t *>(bq + (q & (kRing - 1)));
+                        rd = (uint32_t)(v >> 32) == (uint32_t)(q + 1);
                     }
                     const uint32_t bal = __ballot_sync(kFull, rd);
                     const int n = (bal == kFull) ? 32 : (__ffs(~bal) - 1);
-                    if (lane < n)
-                        reinterpret_cast<uint32_t *>(smem + lay.srcring)[q & (kSrcSlots - 1)] = (uint32_t)v;
+                    for (int k = 0; k < n; ++k) {
+                        const uint32_t lsb = __brev(__shfl_sync(kFull, (uint32_t)v, k));  // bit t = column 32(qb+k) + t
+                        if (P.bottom) {
+                            const int64_t col = (int64_t)(qb + k) * 32 + lane;
+                            if (col < P.S) P.bottom[col + 1] = run + __popc(lsb & ((2u << lane) - 1u));
+                        }
+                        run += __popc(lsb);
+                    }
                     if (n > 0) {
+                        qb += n;
                         __syncwarp();
-                        qs += n;
-                        if (lane == 0) st_release_shared(prod_src, (int)qs);
+                        if (lane == 0) st_release_shared(cons_s + 4u * (uint32_t)W, qb);
                         progress = true;
                     }
                 }
@@ -244,33 +382,32 @@ __global__ void __launch_bounds__(256, 1) k_pair_bp(const PairArgs P) {
                     t_idle = global_ns();
                     idle = 0;
                 } else {
-                    if (ld_relaxed_i32(P.err) != 0) break;
-                    if ((long long)(global_ns() - t_idle) > P.wait_limit_ns) {
-                        raise_error(P.err, kEtimeout);
-                        break;
+                    ++idle;
+                    if ((idle & 15) == 0) {
+                        if (ld_relaxed_i32(P.err) != 0) { ok = false; break; }
+                        if ((long long)(global_ns() - t_idle) > P.wait_limit_ns) {
+                            raise_error(P.err, kEtimeout);
+                            ok = false;
+                            break;
+                        }
                     }
-                    if (++idle > 64) __nanosleep(64);  // spin first: the hand-off is on the critical path
+                    if (idle > 4) __nanosleep(idle > 64 ? 256 : 32);
                 }
             }
+            if (ok && last_strip && lane == 0 && P.len) P.len[0] = run;
             continue;
         }
 
         // ---------------- compute warps ----------------
-        int64_t row0, row1;
-        if (P.strip_row0) {
-            row0 = P.strip_row0[s];
-            row1 = P.strip_row0[s + 1];
-        } else {  // the balanced split in granules of one lane's rows, computed in place
-            const int64_t q = P.granules / P.nstrips, r = P.granules % P.nstrips;
-            row0 = min(P.L, (int64_t)kRowsLane * ((int64_t)s * q + min((int64_t)s, r)));
-            row1 = min(P.L, (int64_t)kRowsLane * ((int64_t)(s + 1) * q + min((int64_t)(s + 1), r)));
-        }
-        const int64_t lbase = row0 + (int64_t)w * (32 * kRowsLane) + (int64_t)lane * kRowsLane;
+        const int64_t wrow0 = row0 + (int64_t)w * (32 * kRowsLane);  // the warp's first row
+        const int64_t lbase = wrow0 + (int64_t)lane * kRowsLane;
         // per word x: first row, real rows, row symbols
         int64_t rbase[WPL];
         int nreal[WPL];
         uint32_t realmask[WPL];
         uint32_t aw[WPL][8];
+        uint32_t Sv[WPL], Yv[WPL];
+        bool badstep = false;
 #pragma unroll
         for (int x = 0; x < WPL; ++x) {
             rbase[x] = lbase + x * kLaneRows;
@@ -290,25 +427,23 @@ __global__ void __launch_bounds__(256, 1) k_pair_bp(const PairArgs P) {
                     pmx[ch * 32 + lane] |= 1u << r;
                 }
             }
-        }
-        // V from the first column's vertical steps (bit set = no step),
-        // padding rows 1, bit 31 held at 1
-        uint32_t Sv[WPL], Yv[WPL];
-        {
-            const int64_t lwords = (P.L + 31) >> 5;
-#pragma unroll
-            for (int x = 0; x < WPL; ++x) {
-                Sv[x] = 0xffffffffu;
-                Yv[x] = 0;
-                if (nreal[x] > 0) {
-                    const int64_t wi = rbase[x] >> 5;
-                    const uint32_t lo = __ldg(P.left_bits + wi);
-                    const uint32_t hi = (wi + 1 < lwords) ? __ldg(P.left_bits + wi + 1) : 0u;
-                    const uint32_t steps = __funnelshift_r(lo, hi, (uint32_t)(rbase[x] & 31)) & realmask[x];
-                    Sv[x] = ~steps;
+            // V from the first column's vertical steps (the left boundary's
+            // unit steps; bit set = no step), padding rows 1, bit 31 held at 1
+            uint32_t steps = 0;
+            if (left != nullptr && nreal[x] > 0) {
+                int32_t prev = left[rbase[x]];
+                for (int r = 0; r < nreal[x]; ++r) {
+                    const int32_t cur = left[rbase[x] + r + 1];
+                    const int32_t d = cur - prev;
+                    badstep |= (d & ~1) != 0;
+                    steps |= (uint32_t)(d & 1) << r;
+                    prev = cur;
                 }
             }
+            Sv[x] = ~steps;
+            Yv[x] = 0;
         }
+        if (badstep) raise_error(P.err, kEinval);
         __syncwarp();
 
         uint32_t cw[WPL], sr[WPL];  // carry-outs (newest in bit 0, never reset); carry-ins (next in bit 31)
@@ -317,91 +452,98 @@ __global__ void __launch_bounds__(256, 1) k_pair_bp(const PairArgs P) {
             cw[x] = 0;
             sr[x] = 0;
         }
-        uint32_t cin_cur = 0;   // the lane above's carry word for this step (sent two steps ago)
-        uint32_t cin_nxt = 0;   // ... and for the next step
+        // the lane above's carry words: for this step, and the two after it
+        uint32_t cin_cur = 0, cin_nxt = 0, cin_n2 = 0;
         uint32_t Mcur[C];       // the upper word's match words for this step
         uint32_t onext[C];      // the next step's column offsets
         uint32_t oprev[C];      // two words: this step's offsets, for the lower word next step
         uint32_t Mlow[C];       // two words: the lower word's match words for this step
         bool ok = true;
-        int cons_seen = 0;  // warps w > 0 downstream: last consumption count read
-        const uint32_t ring_tag0 = 1;
-        // 32-bit word and column indices in the loop (S < 2^31 columns)
-        for (int u = 0; u < (int)nouter; ++u) {
-            // inputs of this word: column offsets up to word u+1, the input carry word u
-            const int need_c = (int)min((int64_t)u + 2, nvwords);
-            const int need_s = (w == 0 && u < nwords) ? (int)(u + 1) : 0;
-            const uint64_t *rw = (w > 0 && u < nwords) ? ring_in + (u % kRing) : nullptr;
-            uint32_t srcw = 0;
-            {
-                bool ready = ld_acquire_shared(prod_cols) >= need_c;
-                if (need_s) ready = ready && ld_acquire_shared(prod_src) >= need_s;
-                uint64_t rv = 0;
-                if (rw) {
-                    rv = *reinterpret_cast<const volatile uint64_t *>(rw);
-                    ready = ready && (uint32_t)(rv >> 32) == (uint32_t)(u + ring_tag0);
+        int cons_seen = 0;      // downstream consumer's progress word, last read
+        uint32_t steps_in = 0;  // set bits of the input carry words: horizontal steps along row wrow0
+        const bool out_shared = (w + 1 < W) || last_strip;
+        uint64_t *dst_row = P.hbuf + (size_t)(s + 1) * P.hstride;
+        // the input carry word of the next 32-column word, read kPrefetch steps
+        // before it is needed (so its load never stalls the column chain)
+        constexpr int kPrefetch = K >= 8 ? K - 4 : 0;
+        auto in_slot = [&](int q) { return in_s + (((uint32_t)q & in_mask) << 3); };
+        uint64_t in_next = nwords > 0 ? lds_u64(in_slot(0)) : 0ull;
+        {   // the first word's offsets and match words (later words: carried over)
+            const uint32_t cb0 = col_ring + (uint32_t)(((-kSk * C * lane) >> 5 & (R - 1)) * 128) +
+                                 (uint32_t)(((-kSk * C * lane) & 31) * 4);
+            uint32_t o0[C];
+            offs_at<C>(cb0, o0);
+            match_words<C>(pm_lane0, o0, Mcur);
+            if constexpr (WPL == 2) {
+                // the lower word's chunk of step 0 (one behind) lies before column 0
+#pragma unroll
+                for (int jj = 0; jj < C; ++jj) {
+                    Mlow[jj] = 0u;
+                    oprev[jj] = o0[jj];
                 }
-                if (!ready) {
-                    if (!wait_inputs(prod_cols, prod_src, need_c, need_s, rw, (uint32_t)(u + ring_tag0), P.err,
-                                     P.wait_limit_ns)) {
+            }
+            offs_at<C>(cb0 + (uint32_t)(C * 4), onext);
+        }
+        for (int u = 0; u < nouter; ++u) {
+            // once per kCheckEvery words, for all of them: the column ring is
+            // filled far enough, and the consumer of this warp's output words
+            // (the next warp, or the producer for the bottom row) has freed the
+            // ring slots they go to.  Conditions are votes, so branches are
+            // warp-uniform.
+            if ((u & (kCheckEvery - 1)) == 0) {
+                const int need_c = min(u + kCheckEvery + 1, nvwords);
+                if (__any_sync(kFull, ld_acquire_shared(prod_cols) < need_c) &&
+                    !wait_cols(prod_cols, need_c, P.err, P.wait_limit_ns)) {
+                    ok = false;
+                    break;
+                }
+                if (out_shared) {
+                    // the last word flushed in these kCheckEvery words
+                    const int wq_hi = (((u + kCheckEvery - 1) * K + kFlushStep - kLag) * C) >> 5;
+                    const int need = min(wq_hi, nwords - 1) - kRing + 1;
+                    if (need > cons_seen) {
+                        if (!__all_sync(kFull, wait_consumed(cons + w + 1, need, P.err, P.wait_limit_ns))) {
+                            ok = false;
+                            break;
+                        }
+                        cons_seen = cons[w + 1];
+                    }
+                }
+            }
+            // the input carry word u: warp 0's from the producer, others' from the warp above
+            uint32_t srcw = 0;
+            if (u < nwords) {
+                uint64_t v = in_next;
+                if (!__all_sync(kFull, (uint32_t)(v >> 32) == (uint32_t)(u + 1))) {
+                    v = wait_tagged(reinterpret_cast<const uint64_t *>(smem + (in_slot(u) - sbase)), (uint32_t)(u + 1),
+                                    P.err, P.wait_limit_ns);
+                    if (!__all_sync(kFull, (uint32_t)(v >> 32) == (uint32_t)(u + 1))) {
                         ok = false;
                         break;
                     }
-                    if (rw) rv = *reinterpret_cast<const volatile uint64_t *>(rw);
                 }
-                if (need_s) srcw = lds_u32(src_ring + (uint32_t)((u & (kSrcSlots - 1)) * 4));
-                else srcw = (uint32_t)rv;
+                srcw = (uint32_t)v;
+                steps_in += __popc(srcw);
             }
-            if (lane == 0) st_release_shared(cons0 + 4u * (uint32_t)w, (int)(u + 1));
+            st_release_shared_if(lane == 0 && (u & (kCheckEvery - 1)) == kCheckEvery - 1, cons_s + 4u * (uint32_t)w,
+                                 u + 1);
             const int ubase = u * K;
             // this lane's column of step 0 (upper word) and its place in the ring
             const int c0 = u * 32 - kSk * C * lane;
             const uint32_t cbase = col_ring + (uint32_t)(((c0 >> 5) & (R - 1)) * 128) + (uint32_t)((c0 & 31) * 4);
-            auto offs_at = [&](uint32_t addr, uint32_t (&o)[C]) {
-                if constexpr (C == 2) {
-                    uint32_t x, y;
-                    asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(x), "=r"(y) : "r"(addr));
-                    o[0] = x;
-                    o[1] = y;
-                } else {
-#pragma unroll
-                    for (int k = 0; k < C / 4; ++k) {
-                        uint32_t x, y, z, v;
-                        asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
-                                     : "=r"(x), "=r"(y), "=r"(z), "=r"(v) : "r"(addr + 16 * k));
-                        o[4 * k] = x;
-                        o[4 * k + 1] = y;
-                        o[4 * k + 2] = z;
-                        o[4 * k + 3] = v;
-                    }
-                }
-            };
             if (lane == 0) sr[0] = srcw;
             // Software pipeline: offsets two steps ahead, match words one step
             // ahead, the carry hand-off after the step's columns (its result is
-            // used two steps later), so a warp issuing in order never waits on
+            // used three steps later), so a warp issuing in order never waits on
             // a shared load or a shuffle before a column.  Columns outside
             // [0, S) read the zero row: no per-lane activity tests.
-            if (u == 0) {  // later words: carried over from the step before
-                uint32_t o0[C];
-                offs_at(cbase, o0);
-                match_words<C>(pm_lane0, o0, Mcur);
-                if constexpr (WPL == 2) {
-                    // the lower word's chunk of step 0 (one behind) lies before column 0
-#pragma unroll
-                    for (int jj = 0; jj < C; ++jj) {
-                        Mlow[jj] = 0u;
-                        oprev[jj] = o0[jj];
-                    }
-                }
-                offs_at(cbase + (uint32_t)(C * 4), onext);
-            }
 #pragma unroll
             for (int i = 0; i < K; ++i) {
                 uint32_t onext2[C], Mnext[C], Mlow_next[C];
-                offs_at(cbase + (uint32_t)((i + 2) * C * 4), onext2);
+                offs_at<C>(cbase + (uint32_t)((i + 2) * C * 4), onext2);
                 match_words<C>(pm_lane0, onext, Mnext);
                 if constexpr (WPL == 2) match_words<C>(pm_lane1, oprev, Mlow_next);
+                if (i == kPrefetch) in_next = (u + 1 < nwords) ? lds_u64(in_slot(u + 1)) : 0ull;
                 if (lane != 0) sr[0] = cin_cur << (32 - C);
                 if constexpr (WPL == 2) {
                     sr[1] = cw[0] << (32 - C);  // the upper word's carries of the step before
@@ -416,7 +558,8 @@ __global__ void __launch_bounds__(256, 1) k_pair_bp(const PairArgs P) {
                 }
                 const uint32_t recv = __shfl_up_sync(kFull, cw[WPL - 1], 1);
                 cin_cur = cin_nxt;
-                cin_nxt = recv;
+                cin_nxt = cin_n2;
+                cin_n2 = recv;
 #pragma unroll
                 for (int jj = 0; jj < C; ++jj) {
                     Mcur[jj] = Mnext[jj];
@@ -426,30 +569,49 @@ __global__ void __launch_bounds__(256, 1) k_pair_bp(const PairArgs P) {
                     }
                     onext[jj] = onext2[jj];
                 }
-                if (i == kFlushStep) {  // lane 31 completes word wq (a predicated store)
+                if (i == kFlushStep) {  // lane 31 completes word wq: predicated stores, no branch
                     const int wq = ((ubase + i - kLag) * C) >> 5;
                     const bool fl = lane == 31 && wq >= 0 && wq < nwords;
-                    if (w + 1 < W) {
-                        // the next warp has consumed up to cons_seen: wait only when
-                        // the ring slot may still be unread.  On a timeout the
-                        // error is raised and every later wait returns at once,
-                        // so the strip ends with its result void.
-                        const int need = (int)(wq - kRing + 1);
-                        if (__any_sync(kFull, fl) && need > cons_seen) {
-                            if (fl) wait_consumed(cons + w + 1, need, P.err, P.wait_limit_ns);
-                            cons_seen = cons[w + 1];
-                        }
-                        st_volatile_shared_u64_if(fl, ring_out_s + (uint32_t)(((wq % kRing) & (kRing - 1)) * 8),
-                                                  ((uint64_t)(uint32_t)(wq + ring_tag0) << 32) | cw[WPL - 1]);
-                    } else {
-                        st_relaxed_u64_if(fl, dst_row + (fl ? wq : 0), ((uint64_t)P.epoch << 32) | cw[WPL - 1]);
-                    }
+                    const uint64_t word = ((uint64_t)(uint32_t)(wq + 1) << 32) | cw[WPL - 1];
+                    // to the next warp or the producer (the slot was checked free) ...
+                    sts_u64_if(fl && out_shared, ring_out_s + (uint32_t)((wq & (kRing - 1)) * 8), word);
+                    // ... or to the next strip, tagged with the launch epoch
+                    st_relaxed_u64_if(fl && !out_shared, dst_row + (fl ? wq : 0),
+                                      ((uint64_t)P.epoch << 32) | cw[WPL - 1]);
+                }
+            }
+        }
+        if (lane == 0) st_release_shared(cons_s + 4u * (uint32_t)w, nouter);
+        // The right column: H[i][S] for this warp's rows, from H[wrow0][S] =
+        // H[wrow0][0] + (horizontal steps along row wrow0) and the lanes'
+        // vertical steps at the last column, in row order (lane-major).
+        if (ok && P.right != nullptr && wrow0 < row1) {
+            uint32_t vbits[WPL];
+            int cnt = 0;
+#pragma unroll
+            for (int x = 0; x < WPL; ++x) {
+                vbits[x] = ~(Sv[x] | Yv[x]) & realmask[x];
+                cnt += __popc(vbits[x]);
+            }
+            int inc = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(kFull, inc, o);
+                if (lane >= o) inc += y;
+            }
+            const int32_t base = (left ? left[wrow0] : 0) + (int32_t)steps_in;
+            if (s == 0 && w == 0 && lane == 0) P.right[0] = base;  // H[0][S]
+            int32_t val = base + inc - cnt;
+#pragma unroll
+            for (int x = 0; x < WPL; ++x) {
+                for (int r = 0; r < nreal[x]; ++r) {
+                    val += (int32_t)((vbits[x] >> r) & 1u);
+                    P.right[rbase[x] + r + 1] = val;
                 }
             }
         }
 #pragma unroll
         for (int x = 0; x < WPL; ++x) {
-            if (ok && nreal[x] > 0) P.right_bits[rbase[x] / kLaneRows] = ~(Sv[x] | Yv[x]) & realmask[x];
             uint32_t *pmx = x == 0 ? pm0 : pm1;
 #pragma unroll
             for (int r = 0; r < kLaneRows; ++r) {
@@ -460,167 +622,15 @@ __global__ void __launch_bounds__(256, 1) k_pair_bp(const PairArgs P) {
             }
         }
     }
-}
-
-// ---------------------------------------------------------------------------
-// boundary conversions
-// ---------------------------------------------------------------------------
-
-// bits[k] word: bit t = v[32k+t+1] - v[32k+t] for 32k+t < len; a step that is
-// not 0/1 is an invalid boundary.  Optionally also writes the epoch-tagged
-// copy (row 0 of the carry buffer).  `other` (may be NULL) is the other
-// boundary, whose element 0 must equal v[0].
-__global__ void k_boundary_bits(const int32_t *v, int64_t len, uint32_t *bits, uint64_t *tagged,
-                                uint32_t epoch, const int32_t *other, int *err) {
-    const int64_t nw = (len + 31) >> 5;
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nw;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        uint32_t word = 0;
-        bool badstep = false;
-        const int64_t base = k * 32;
-        const int nb = (int)min((int64_t)32, len - base);
-        int32_t prev = v[base];
-        for (int t = 0; t < nb; ++t) {
-            const int32_t cur = v[base + t + 1];
-            const int32_t d = cur - prev;
-            if (d != 0 && d != 1) badstep = true;
-            word |= (uint32_t)(d & 1) << t;
-            prev = cur;
+    // The last CTA to leave resets the strip ticket and the exit count, so the
+    // next launch on the stream starts from zero without a separate memset.
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const int d = atomicAdd(P.ctl + 1, 1);
+        if (d == (int)gridDim.x - 1) {
+            atomicExch(P.ctl, 0);
+            atomicExch(P.ctl + 1, 0);
         }
-        if (badstep) atomicCAS(err, 0, kEinval);
-        if (bits) bits[k] = word;
-        if (tagged) tagged[k] = ((uint64_t)epoch << 32) | __brev(word);
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0 && other != nullptr && other[0] != v[0])
-        atomicCAS(err, 0, kEinval);
-}
-
-__global__ void k_tag_zero(uint64_t *tagged, int64_t nw, uint32_t epoch) {
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nw;
-         k += (int64_t)gridDim.x * blockDim.x)
-        tagged[k] = (uint64_t)epoch << 32;
-}
-
-// Prefix of step bits.  Pass 1: popcount per block of kPB words.
-constexpr int kPB = 1024;
-
-__device__ __forceinline__ uint32_t load_bits_word(const uint32_t *bits, const uint64_t *tagged,
-                                                   int64_t k) {  // tagged words are MSB-first columns
-    return bits ? bits[k] : __brev((uint32_t)tagged[k]);
-}
-
-template <int BPW>
-__global__ void k_prefix_pass1(const uint32_t *bits, const uint64_t *tagged, int64_t nbits,
-                               int64_t *block_sums) {
-    __shared__ int64_t red[32];
-    const int64_t nw = (nbits + BPW - 1) / BPW;
-    const int64_t k = blockIdx.x * (int64_t)kPB + threadIdx.x;
-    uint32_t c = 0;
-    if (k < nw) {
-        uint32_t word = load_bits_word(bits, tagged, k);
-        const int64_t rem = nbits - k * BPW;
-        if (rem < 32) word &= (1u << rem) - 1u;
-        c = __popc(word);
-    }
-    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(kFull, c, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        int64_t x = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0;
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(kFull, x, o);
-        if (threadIdx.x == 0) block_sums[blockIdx.x] = x;
-    }
-}
-
-// Pass 2: exclusive scan of the block sums (one block, sequential chunks).
-__global__ void k_prefix_pass2(int64_t *block_sums, int64_t nblocks) {
-    __shared__ int64_t carry;
-    __shared__ int64_t warp_tot[32];
-    if (threadIdx.x == 0) carry = 0;
-    __syncthreads();
-    for (int64_t base = 0; base < nblocks; base += blockDim.x) {
-        const int64_t i = base + threadIdx.x;
-        int64_t x = i < nblocks ? block_sums[i] : 0;
-        // inclusive warp scan
-        int64_t inc = x;
-        for (int o = 1; o < 32; o <<= 1) {
-            const int64_t y = __shfl_up_sync(kFull, inc, o);
-            if ((threadIdx.x & 31) >= o) inc += y;
-        }
-        if ((threadIdx.x & 31) == 31) warp_tot[threadIdx.x >> 5] = inc;
-        __syncthreads();
-        if (threadIdx.x < 32) {
-            int64_t t = threadIdx.x < (blockDim.x >> 5) ? warp_tot[threadIdx.x] : 0;
-            int64_t ti = t;
-            for (int o = 1; o < 32; o <<= 1) {
-                const int64_t y = __shfl_up_sync(kFull, ti, o);
-                if (threadIdx.x >= o) ti += y;
-            }
-            warp_tot[threadIdx.x] = ti - t;  // exclusive
-        }
-        __syncthreads();
-        const int64_t excl = carry + warp_tot[threadIdx.x >> 5] + inc - x;
-        if (i < nblocks) block_sums[i] = excl;
-        __syncthreads();
-        if (threadIdx.x == blockDim.x - 1) carry = excl + x;
-        __syncthreads();
-    }
-}
-
-// Pass 3: out[0] = base; out[i+1] = base + (number of set bits among the first i+1).
-// A word holds BPW elements (32 for packed bit rows, 31 for lane words).
-template <int BPW>
-__global__ void k_prefix_pass3(const uint32_t *bits, const uint64_t *tagged, int64_t nbits,
-                               const int64_t *block_excl, const int32_t *base_ptr,
-                               int64_t base_index, int32_t *out, int32_t *len_out) {
-    __shared__ uint32_t words[kPB];
-    __shared__ int32_t wpre[kPB];
-    __shared__ int32_t warp_tot[32];
-    const int64_t nw = (nbits + BPW - 1) / BPW;
-    const int64_t k0 = blockIdx.x * (int64_t)kPB;
-    const int64_t k = k0 + threadIdx.x;
-    uint32_t word = 0;
-    if (k < nw) {
-        word = load_bits_word(bits, tagged, k);
-        const int64_t rem = nbits - k * BPW;
-        if (rem < 32) word &= (1u << rem) - 1u;
-    }
-    words[threadIdx.x] = word;
-    const int32_t c = __popc(word);
-    int32_t inc = c;
-    for (int o = 1; o < 32; o <<= 1) {
-        const int32_t y = __shfl_up_sync(kFull, inc, o);
-        if ((threadIdx.x & 31) >= o) inc += y;
-    }
-    if ((threadIdx.x & 31) == 31) warp_tot[threadIdx.x >> 5] = inc;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        const int32_t t = threadIdx.x < (blockDim.x >> 5) ? warp_tot[threadIdx.x] : 0;
-        int32_t ti = t;
-        for (int o = 1; o < 32; o <<= 1) {
-            const int32_t y = __shfl_up_sync(kFull, ti, o);
-            if (threadIdx.x >= o) ti += y;
-        }
-        warp_tot[threadIdx.x] = ti - t;
-    }
-    __syncthreads();
-    wpre[threadIdx.x] = warp_tot[threadIdx.x >> 5] + inc - c;
-    __syncthreads();
-    const int32_t base0 = base_ptr ? base_ptr[base_index] : 0;
-    const int32_t base = base0 + (int32_t)block_excl[blockIdx.x];
-    if (out != nullptr) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) out[0] = base0;
-        const int64_t nb_here = min((int64_t)kPB * BPW, nbits - k0 * BPW);
-        for (int64_t idx = threadIdx.x; idx < nb_here; idx += blockDim.x) {
-            const int wl = (int)(idx / BPW);
-            const int b = (int)(idx - (int64_t)wl * BPW);
-            const uint32_t mask = b == 31 ? kFull : ((2u << b) - 1u);
-            out[k0 * BPW + idx + 1] = base + wpre[wl] + __popc(words[wl] & mask);
-        }
-    }
-    if (len_out != nullptr && blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
-        const int wl = (int)(nw - 1 - k0);
-        len_out[0] = base + wpre[wl] + __popc(words[wl]);
     }
 }
 
@@ -742,6 +752,7 @@ int pair_occupancy(int C, int warps, int wpl) {
 }
 
 cudaError_t launch_pair_bp(const PairArgs &p, int C, int warps, int wpl, int grid, cudaStream_t st) {
+    if (warps < 1 || warps > 7 || grid < 1 || p.nstrips < 1) return cudaErrorInvalidValue;
     if (wpl == 2) {
         switch (C) {
             case 2: return launch_cw<2, 2>(p, warps, grid, st);
@@ -756,50 +767,6 @@ cudaError_t launch_pair_bp(const PairArgs &p, int C, int warps, int wpl, int gri
         case 8: return launch_cw<8, 1>(p, warps, grid, st);
         default: return cudaErrorInvalidValue;
     }
-}
-
-cudaError_t launch_boundary_bits(const int32_t *v, int64_t len, uint32_t *bits, uint64_t *tagged,
-                                 uint32_t epoch, const int32_t *other, int *err, cudaStream_t st) {
-    const int64_t nw = (len + 31) >> 5;
-    if (v == nullptr) {
-        if (bits && nw) {
-            cudaError_t e = cudaMemsetAsync(bits, 0, nw * sizeof(uint32_t), st);
-            if (e != cudaSuccess) return e;
-        }
-        if (tagged && nw) {
-            const int grid = (int)min((int64_t)1024, (nw + 255) / 256);
-            k_tag_zero<<<grid, 256, 0, st>>>(tagged, nw, epoch);
-            return cudaGetLastError();
-        }
-        return cudaSuccess;
-    }
-    if (nw == 0) {
-        if (other) k_boundary_bits<<<1, 32, 0, st>>>(v, 0, nullptr, nullptr, epoch, other, err);
-        return cudaGetLastError();
-    }
-    const int grid = (int)min((int64_t)2048, (nw + 255) / 256);
-    k_boundary_bits<<<grid, 256, 0, st>>>(v, len, bits, tagged, epoch, other, err);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_bits_prefix(const uint32_t *bits, const uint64_t *tagged, int64_t nbits, int bpw,
-                               const int32_t *base_ptr, int64_t base_index, int32_t *out,
-                               int32_t *len_out, PrefixScratch &scr, cudaStream_t st) {
-    const int64_t nw = (nbits + bpw - 1) / bpw;
-    const int64_t nblocks = (nw + kPB - 1) / kPB;
-    if (nblocks == 0 || nblocks > scr.cap || (bpw != 31 && bpw != 32)) return cudaErrorInvalidValue;
-    if (bpw == 32) {
-        k_prefix_pass1<32><<<(unsigned)nblocks, kPB, 0, st>>>(bits, tagged, nbits, scr.block_sums);
-        k_prefix_pass2<<<1, 1024, 0, st>>>(scr.block_sums, nblocks);
-        k_prefix_pass3<32><<<(unsigned)nblocks, kPB, 0, st>>>(bits, tagged, nbits, scr.block_sums,
-                                                              base_ptr, base_index, out, len_out);
-    } else {
-        k_prefix_pass1<31><<<(unsigned)nblocks, kPB, 0, st>>>(bits, tagged, nbits, scr.block_sums);
-        k_prefix_pass2<<<1, 1024, 0, st>>>(scr.block_sums, nblocks);
-        k_prefix_pass3<31><<<(unsigned)nblocks, kPB, 0, st>>>(bits, tagged, nbits, scr.block_sums,
-                                                              base_ptr, base_index, out, len_out);
-    }
-    return cudaGetLastError();
 }
 
 cudaError_t launch_degenerate(const int32_t *top, const int32_t *left, int64_t n, int64_t m,

@@ -178,14 +178,14 @@ bool plan_pair(int64_t n, int64_t m, int sms, const PairPlanOptions &o, PairPlan
     out.C = o.chunk ? o.chunk : ((out.S >= 64) ? 2 : 4);
     // words per lane: each lane streams all S columns after a fill of
     // (lanes x skew x C) column steps; two words per lane halve the lanes and
-    // take a longer skew and step (measured: 1.18x the step time, skew 3
-    // chunks against 2).  Pick the smaller modelled time.
+    // take a longer skew and step (skew 4 chunks against 3; the step's time
+    // ratio is measured on GB300).  Pick the smaller modelled time.
     if (o.wpl == 1 || o.wpl == 2) {
         out.wpl = o.wpl;
     } else {
         auto cost = [&](int wpl) {
             const double lanes = (double)((out.L + kPlanLaneRows * wpl - 1) / (kPlanLaneRows * wpl));
-            const double skew = wpl == 1 ? 2.0 : 3.0, step = wpl == 1 ? 1.0 : 1.18;
+            const double skew = wpl == 1 ? 3.0 : 4.0, step = wpl == 1 ? 1.0 : 1.18;
             return step * ((double)out.S + lanes * skew * out.C);
         };
         out.wpl = cost(2) < cost(1) ? 2 : 1;
@@ -193,14 +193,15 @@ bool plan_pair(int64_t n, int64_t m, int sms, const PairPlanOptions &o, PairPlan
     const int64_t warp_rows = kPlanWarpRows * out.wpl, lane_rows = kPlanLaneRows * out.wpl;
     const int64_t warps_total = (out.L + warp_rows - 1) / warp_rows;
     // one warp per CTA strip unless the strips would not all be resident at once
+    const int max_w = out.wpl == 2 ? o.max_warps_wpl2 : o.max_warps;
     int W = o.warps > 0 ? o.warps : 1;
-    W = std::max(1, std::min(W, o.max_warps));
+    W = std::max(1, std::min(W, max_w));
     if ((int64_t)W > warps_total) W = (int)warps_total;
     int64_t nstrips = (warps_total + W - 1) / W;
     if (o.warps == 0 && o.resident > 0 && nstrips > o.resident) {
         // keep every strip resident when shared memory allows taller CTA strips
         const int64_t need = (warps_total + o.resident - 1) / o.resident;
-        if (need <= o.max_warps) {
+        if (need <= max_w) {
             W = (int)need;
             nstrips = (warps_total + W - 1) / W;
         }

@@ -60,7 +60,8 @@ struct PairPlanOptions {
     int orient = 0;     // 0: bits along the longer string; 1: along a; 2: along b
     int schedule = 0;   // 0: balanced strips (p-way split); 1: uniform strips of W*992*wpl rows
     int wpl = 0;        // 31-row words per lane: 0 = planner, 1 or 2
-    int max_warps = 7;  // shared-memory limit per CTA
+    int max_warps = 7;       // shared-memory limit per CTA with one word per lane
+    int max_warps_wpl2 = 3;  // ... and with two words per lane (twice the match tables)
     int resident = 0;   // CTAs that fit on the device at once (0: unknown)
 };
 

@@ -223,7 +223,14 @@ void worker_main(ServeEngine *E) {
     for (;;) {
         // completions
         for (auto &S : E->slots) {
-            if (S.busy && cudaEventQuery(S.done) == cudaSuccess) complete_slot(E, S, PACO_OK);
+            if (S.busy && cudaEventQuery(S.done) == cudaSuccess) {
+                const auto t0 = std::chrono::steady_clock::now();
+                complete_slot(E, S, PACO_OK);
+                const uint64_t ns = (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
+                                        std::chrono::steady_clock::now() - t0).count();
+                std::lock_guard<std::mutex> lk(E->mu);
+                E->stats.host_complete_ns += ns;
+            }
         }
         // admission: fill one free slot from the queue
         Slot *free_slot = nullptr;
@@ -262,7 +269,14 @@ void worker_main(ServeEngine *E) {
             free_slot->busy = true;
             E->stats.batches_launched += 1;
         }
+        const auto t0 = std::chrono::steady_clock::now();
         const int rc = launch_slot(E, *free_slot);
+        const uint64_t ns = (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
+                                std::chrono::steady_clock::now() - t0).count();
+        {
+            std::lock_guard<std::mutex> lk(E->mu);
+            E->stats.host_launch_ns += ns;
+        }
         if (rc != PACO_OK) complete_slot(E, *free_slot, rc);
     }
 }

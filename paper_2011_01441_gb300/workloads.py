@@ -277,3 +277,39 @@ def poisson_arrivals(seed: int, count: int, rate_per_s: float) -> np.ndarray:
     u = unit(seed, 3, count)
     gaps = -np.log1p(-u) / rate_per_s
     return np.cumsum(gaps)
+
+
+def _serve_chunk(args):
+    k0, k1, seed = args
+    reqs = [serve_request(k, seed=seed) for k in range(k0, k1)]
+    a_cat, a_off = _concat([r.a for r in reqs])
+    b_cat, b_off = _concat([r.b for r in reqs])
+    return k0, a_cat, a_off, b_cat, b_off
+
+
+def serve_stream(count: int = 100000, seed: int = 5, workers: int = 0, chunk: int = 2000) -> Batch:
+    """Requests 0..count-1 of the serving stream (the same bytes as
+    serve_request(k) one by one), concatenated like a batch.  With workers > 1
+    the chunks are made by a process pool started with `spawn` (safe in a
+    process that already uses CUDA); the result does not depend on it."""
+    jobs = [(k, min(count, k + chunk), seed) for k in range(0, count, chunk)]
+    if workers > 1 and len(jobs) > 1:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(min(workers, len(jobs))) as pool:
+            parts = pool.map(_serve_chunk, jobs)
+    else:
+        parts = [_serve_chunk(j) for j in jobs]
+    parts.sort(key=lambda x: x[0])
+    a_cat = np.concatenate([p[1] for p in parts]) if parts else np.zeros(0, np.uint8)
+    b_cat = np.concatenate([p[3] for p in parts]) if parts else np.zeros(0, np.uint8)
+    a_off = np.zeros(count + 1, dtype=np.int64)
+    b_off = np.zeros(count + 1, dtype=np.int64)
+    k = 0
+    for p in parts:
+        n = p[2].size - 1
+        a_off[k + 1:k + n + 1] = a_off[k] + p[2][1:]
+        b_off[k + 1:k + n + 1] = b_off[k] + p[4][1:]
+        k += n
+    return Batch(a_cat, a_off, b_cat, b_off,
+                 f"serving stream: {count} requests, lengths log-uniform [32, 65536], sigma 20, "
+                 f"half 20%-mutated (seed {seed})")

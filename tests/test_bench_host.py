@@ -101,11 +101,16 @@ def test_profiled_traffic_only_while_the_kernel_source_is_unchanged(tmp_path, mo
     csrc.mkdir(parents=True)
     for f in ("pair_kernels.cu", "bp_device.cuh"):
         shutil.copy(os.path.join(ROOT, "paper_2011_01441_gb300", "csrc", f), csrc / f)
-    shutil.copy(os.path.join(ROOT, "profiles", "k_pair_bp_pair131072_launches.md"), root / "profiles")
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("pair_kernels.cu", "bp_device.cuh"):
+        h.update((csrc / f).read_bytes())
+    (root / "profiles" / "k_pair_bp_pair131072_launches.md").write_text(
+        f"# a summary\n\nsource_sha256: {h.hexdigest()}\ntraffic_bytes_per_launch: 4753408\n")
     monkeypatch.setattr(bench_mod, "ROOT", str(root))
     srcs = ["pair_kernels.cu", "bp_device.cuh"]
     committed = bench_mod._profiled_traffic("k_pair_bp_pair131072_launches.md", srcs)
-    assert isinstance(committed, int) and committed > 0
+    assert committed == 4753408
     with open(csrc / "bp_device.cuh", "a") as f:
         f.write("\n// an edit after the capture\n")
     assert bench_mod._profiled_traffic("k_pair_bp_pair131072_launches.md", srcs) is None
