@@ -315,42 +315,33 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def run_gpu(args):
+def _pair_timing(P, ctx, pair, steps, warmup, dev, stream, flush, rank_sync=False):
+    """Timed steps of one pair through paco_lcs_boundaries (inputs resident,
+    L2 flushed between steps): per-step CUDA-event times, the library's own
+    event time of the kernel, the host time of each call, and the clocks."""
     import torch
-    import paper_2011_01441_gb300 as P
-
-    ws, rank, local = _dist()
-    _init_dist(ws, local)
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    P.load()
-    ctx = P.Context(local)
-    pair, desc = _workload(args.config)
     n, m = pair.a.size, pair.b.size
     da = torch.from_numpy(pair.a).to(dev)
     db = torch.from_numpy(pair.b).to(dev)
     row = torch.empty(m + 1, dtype=torch.int32, device=dev)
     col = torch.empty(n + 1, dtype=torch.int32, device=dev)
     L = torch.empty(1, dtype=torch.int32, device=dev)
-    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
-    stream = torch.cuda.current_stream()
 
     def step():
         P.paco_lcs_boundaries(ctx, da, db, bottom_row=row, right_col=col, length=L, stream=stream)
 
     h0 = time.perf_counter()
-    step()  # the first call plans, uploads the plan and sizes the context's scratch
+    step()  # the first call plans and sizes the context's scratch
     first_us = (time.perf_counter() - h0) * 1e6
-    for _ in range(args.warmup - 1):
+    for _ in range(warmup - 1):
         step()
     ctx.sync()
-    kernel_ms = []
-    step_ms = []
-    host_us = []  # host time of the call itself: cached plan + launches, no wait on the GPU
-    _barrier()
+    kernel_ms, step_ms, host_us = [], [], []
+    if rank_sync:
+        _barrier()
     torch.cuda.synchronize()
-    with ClockSampler(local) as clocks:
-        for _ in range(args.steps):
+    with ClockSampler(dev.index or 0) as clocks:
+        for _ in range(steps):
             flush.fill_(1)  # evict the inputs from L2 between timed steps
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
@@ -363,8 +354,72 @@ def run_gpu(args):
             step_ms.append(e0.elapsed_time(e1))
             kernel_ms.append(P.paco_last_kernel_ms(ctx)[0])
         torch.cuda.synchronize()
-    _barrier()
+    if rank_sync:
+        _barrier()
     ctx.sync()
+    return {"kernel_ms": kernel_ms, "step_ms": step_ms, "host_us": host_us, "first_us": first_us,
+            "clocks": clocks.summary(), "L": L}
+
+
+def _pair_model(plan, kmed, clk):
+    """The critical-path model of the strip pipeline: every lane streams all S
+    columns, and lane k starts skew x C columns after lane k-1 (skew 3 chunks
+    with one word per lane, 4 with two), at the column chain's latency."""
+    sm_hz = (clk["sm_mhz"] if clk else 2070.0) * 1e6
+    wpl = plan.get("words_per_lane", 1)
+    lanes = (plan["L"] + 31 * wpl - 1) // (31 * wpl)
+    cp_steps = plan["S"] + (3 if wpl == 1 else 4) * plan["chunk"] * lanes
+    cp_ms = cp_steps * CHAIN_CYCLES_PER_COLUMN / sm_hz * 1e3
+    return {"bound": "dependency chain", "model_ms": cp_ms, "measured_ms": kmed, "frac": cp_ms / kmed,
+            "column_steps": cp_steps, "cycles_per_column": CHAIN_CYCLES_PER_COLUMN,
+            "measured_cycles_per_column_step": kmed * 1e-3 * sm_hz / cp_steps,
+            "note": "one lane streams all S columns; lanes trail by 3 (one word per lane) or 4 (two words) "
+                    "chunks each"}
+
+
+def pair_record(P, ctx, name, steps, warmup, dev, stream, flush, peak_ops, sms):
+    """A nested record for another single-pair workload (the 4096 pair, the
+    1048576 x 16384 pair): GCUPS, kernel and step times, launches per step,
+    roofline fractions and its own clock record."""
+    pair, desc = _workload(name)
+    n, m = pair.a.size, pair.b.size
+    t = _pair_timing(P, ctx, pair, steps, warmup, dev, stream, flush)
+    cells = float(n) * m
+    kmed = statistics.median(t["kernel_ms"])
+    plan = P.paco_plan_pair(n, m, sms)
+    word_steps = (plan["L"] + 30) // 31 * plan["S"]
+    return {"value": cells * steps / (sum(t["step_ms"]) * 1e-3) / 1e9, "unit": "GCUPS", "steps": steps,
+            "warmup": warmup, "ms_per_step": sum(t["step_ms"]) / steps,
+            "config": {"workload": desc, "n": n, "m": m, "chunk": plan["chunk"], "warps_per_cta": plan["warps"],
+                       "strips": plan["nstrips"], "words_per_lane": plan.get("words_per_lane", 1),
+                       "l2": "flushed between timed steps (512 MiB write)"},
+            "kernel_ms_median": kmed, "kernel_ms_min": min(t["kernel_ms"]),
+            "host_call_us_median": statistics.median(t["host_us"]), "host_first_call_us": t["first_us"],
+            "gpu_launches_per_step": 1,
+            "roofline": {"bound": "alu", "frac": cells * CELL_OPS / (kmed * 1e-3) / peak_ops,
+                         "achieved": cells * CELL_OPS / (kmed * 1e-3) / 1e12, "peak": peak_ops / 1e12,
+                         "unit": "Tops/s (int32 lane-ops, 4 per cell)", "kernel": "k_pair_bp"},
+            "roofline_bitparallel": {"frac": word_steps * OPS_PER_WORD_STEP / (kmed * 1e-3) / peak_ops},
+            "critical_path": _pair_model(plan, kmed, t["clocks"]),
+            "clocks": t["clocks"]}
+
+
+def run_gpu(args):
+    import torch
+    import paper_2011_01441_gb300 as P
+
+    ws, rank, local = _dist()
+    _init_dist(ws, local)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    P.load()
+    ctx = P.Context(local)
+    pair, desc = _workload(args.config)
+    n, m = pair.a.size, pair.b.size
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    t = _pair_timing(P, ctx, pair, args.steps, args.warmup, dev, stream, flush, rank_sync=True)
+    kernel_ms, step_ms, host_us, clk = t["kernel_ms"], t["step_ms"], t["host_us"], t["clocks"]
     tot_ms = _max_over_ranks(sum(step_ms), dev)
     cells = float(n) * m
     value = weak_scaling_value(cells, ws, args.steps, tot_ms)
@@ -376,7 +431,7 @@ def run_gpu(args):
     hcol = torch.empty(n + 1, dtype=torch.int32).pin_memory()
     hlen = torch.empty(1, dtype=torch.int32)
     import ctypes
-    vp = lambda t: ctypes.c_void_p(t.data_ptr())
+    vp = lambda x: ctypes.c_void_p(x.data_ptr())
     P.paco_lcs_boundaries_host_ptr(ctx, vp(ha), n, vp(hb), m, vp(hrow), vp(hcol), vp(hlen))
     e2e_t = []
     for _ in range(max(3, args.steps)):
@@ -386,22 +441,17 @@ def run_gpu(args):
         P.paco_lcs_boundaries_host_ptr(ctx, vp(ha), n, vp(hb), m, vp(hrow), vp(hcol), vp(hlen))
         e2e_t.append(time.perf_counter() - t0)
     e2e_val = cells / statistics.median(e2e_t) / 1e9
-    assert int(hlen.item()) == int(L.item())
+    assert int(hlen.item()) == int(t["L"].item())
 
     # roofline of the dominant kernel: measured integer-ALU issue rate
     peak_ops = P.paco_measure_int_peak(ctx, 0)
     kmed = statistics.median(kernel_ms)
-    plan = P.paco_plan_pair(n, m, torch.cuda.get_device_properties(dev).multi_processor_count)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    plan = P.paco_plan_pair(n, m, sms)
     word_steps = (plan["L"] + 30) // 31 * plan["S"]
     achieved_bp = word_steps * OPS_PER_WORD_STEP / (kmed * 1e-3)
     achieved = cells * CELL_OPS / (kmed * 1e-3)
     peaks = _peaks()
-    clk = clocks.summary()
-    sm_hz = (clk["sm_mhz"] if clk else 2070.0) * 1e6
-    wpl = plan.get("words_per_lane", 1)
-    lanes = (plan["L"] + 31 * wpl - 1) // (31 * wpl)
-    cp_steps = plan["S"] + (2 if wpl == 1 else 3) * plan["chunk"] * lanes
-    cp_ms = cp_steps * CHAIN_CYCLES_PER_COLUMN / sm_hz * 1e3
     traffic = _profiled_traffic("k_pair_bp_pair131072_launches.md", ["pair_kernels.cu", "bp_device.cuh"]) \
         if args.config == "mutated" else None
     if rank != 0:
@@ -410,14 +460,14 @@ def run_gpu(args):
         "metric": METRIC, "value": value, "unit": "GCUPS", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": desc, "n": n, "m": m, "engine": "bit-parallel strip pipeline",
+        "config": {"workload": desc, "n": n, "m": m, "engine": "bit-parallel strip pipeline, one launch",
                    "chunk": plan["chunk"], "warps_per_cta": plan["warps"], "strips": plan["nstrips"],
                    "words_per_lane": plan.get("words_per_lane", 1),
                    "l2": "flushed between timed steps (512 MiB write)"},
         "kernel_ms_median": kmed,
         "kernel_ms_min": min(kernel_ms),
         "host_call_us_median": statistics.median(host_us),
-        "host_first_call_us": first_us,
+        "host_first_call_us": t["first_us"],
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                      "unit": "Tops/s (int32 lane-ops, 4 per cell)", "frac": achieved / peak_ops,
                      "traffic": traffic, "kernel": "k_pair_bp", "ops_per_cell": CELL_OPS,
@@ -427,21 +477,28 @@ def run_gpu(args):
                                  "frac": achieved_bp / peak_ops,
                                  "note": "lane-ops the bit-parallel recurrence itself needs (4 per 31-row word "
                                          "and column) over the same peak"},
-        "critical_path": {"bound": "dependency chain", "model_ms": cp_ms, "measured_ms": kmed,
-                          "frac": cp_ms / kmed, "column_steps": cp_steps,
-                          "cycles_per_column": CHAIN_CYCLES_PER_COLUMN,
-                          "note": "one lane streams all S columns; lanes trail by 2 (one word per lane) "
-                                  "or 3 (two words) chunks each"},
+        "critical_path": _pair_model(plan, kmed, clk),
         "e2e": {"value": e2e_val, "unit": "GCUPS", "h2d_bytes_per_step": n + m,
                 "d2h_bytes_per_step": 4 * (n + 1) + 4 * (m + 1) + 4},
-        "gpu_launches": 8 * args.steps,
+        "gpu_launches": args.steps,  # k_pair_bp: the whole step is one launch
         "clocks": clk,
         "hbm_peak_gbs_measured": peaks.get("hbm_gbs"),
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_pair(pair.a, pair.b)
+    if ws == 1 and args.config == "mutated" and not args.headline_only:
+        # the other workloads of the metric, each with its own clock record
+        line["small"] = pair_record(P, ctx, "small", DEFAULT_STEPS["small"], args.warmup, dev, stream, flush,
+                                    peak_ops, sms)
+        line["skinny"] = pair_record(P, ctx, "skinny", 100, args.warmup, dev, stream, flush, peak_ops, sms)
+        ctx.close()
+        del flush
+        torch.cuda.empty_cache()
+        line["batch"] = batch_record(200, max(3, args.warmup))
+        line["served"] = served_record(100000)
+    else:
+        ctx.close()
     print(json.dumps(line), flush=True)
-    ctx.close()
 
 
 def _chunks_by_class(packed):
@@ -450,9 +507,9 @@ def _chunks_by_class(packed):
     return {nm: (int(packed) >> (4 * k)) & 15 for k, nm in enumerate(names)}
 
 
-def run_batch_bench(args):
-    """The 4096-pair batch through paco_lcs_batch (one graph replay per step)
-    against the single-pair path called once per pair."""
+def batch_record(steps, warmup, plain=True):
+    """The 4096-pair batch through paco_lcs_batch (one graph replay per step),
+    against the single-pair path called once per pair.  Returns the record."""
     import torch
     import paper_2011_01441_gb300 as P
     P.load()
@@ -463,12 +520,17 @@ def run_batch_bench(args):
     db = torch.from_numpy(bt.b_cat).cuda()
     L = torch.empty(bt.npairs, dtype=torch.int32, device="cuda")
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
-    for _ in range(args.warmup):  # the first call plans, autotunes and captures the graph
+    torch.cuda.synchronize()
+    h0 = time.perf_counter()  # the first call plans, autotunes the chunk widths and captures the graph
+    P.paco_lcs_batch(ctx, da, db, bt.a_off, bt.b_off, lengths=L)
+    ctx.sync()
+    first_ms = (time.perf_counter() - h0) * 1e3
+    for _ in range(max(0, warmup - 1)):
         P.paco_lcs_batch(ctx, da, db, bt.a_off, bt.b_off, lengths=L)
     ctx.sync()
     ms = []
     with ClockSampler(0) as clocks:
-        for _ in range(args.steps):
+        for _ in range(steps):
             flush.fill_(1)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
@@ -478,135 +540,181 @@ def run_batch_bench(args):
             ms.append(e0.elapsed_time(e1))
     ctx.sync()
     cells = bt.cells()
-    value = cells * args.steps / (sum(ms) * 1e-3) / 1e9
+    value = cells * steps / (sum(ms) * 1e-3) / 1e9
     # plain: one pair per launch on one stream, same pairs
-    plain_s = float("nan")
-    lens = torch.empty(1, dtype=torch.int32, device="cuda")
-    if not args.no_plain:
+    plain_rec = None
+    if plain:
+        lens = torch.empty(1, dtype=torch.int32, device="cuda")
         views = [(da[bt.a_off[k]:bt.a_off[k + 1]], db[bt.b_off[k]:bt.b_off[k + 1]]) for k in range(bt.npairs)]
+        for a, b in views[:64]:
+            P.paco_lcs_length(ctx, a, b, out=lens)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for a, b in views:
             P.paco_lcs_length(ctx, a, b, out=lens)
         torch.cuda.synchronize()
         plain_s = time.perf_counter() - t0
+        plain_rec = {"value": cells / plain_s / 1e9, "unit": "GCUPS", "seconds": plain_s,
+                     "method": "paco_lcs_length once per pair on one stream (one launch each)"}
     peak_ops = P.paco_measure_int_peak(ctx, 0)
     med = statistics.median(ms)
     word_steps = sum(((max(n, m) + 30) // 31) * min(n, m) for n, m in zip(np.diff(bt.a_off), np.diff(bt.b_off)))
     achieved_bp = word_steps * OPS_PER_WORD_STEP / (med * 1e-3)
     achieved = cells * CELL_OPS / (med * 1e-3)
-    line = {"metric": METRIC, "value": value, "unit": "GCUPS", "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": sum(ms) / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": bt.name + " (seed 4)", "pairs": bt.npairs, "cells": cells,
-                       "engine": "batch graph, warp jobs", "alphabet": 4, "chunk_by_class": _chunks_by_class(ctx.get_option(P.OPT_BATCH_CHUNKS)),
-                       "l2": "flushed between timed steps"},
-            "step_ms_median": med, "step_ms_min": min(ms),
-            "plain_one_pair_per_launch": None if args.no_plain else
-            {"value": cells / plain_s / 1e9, "unit": "GCUPS", "seconds": plain_s},
-            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
-                         "unit": "Tops/s (int32 lane-ops, 4 per cell)", "frac": achieved / peak_ops,
-                         "traffic": _profiled_traffic("k_batch_batch4096_full.md", ["batch.cu", "bp_device.cuh"]),
-                         "duration": "whole step (column offsets + k_batch + prefixes), an upper bound on k_batch",
-                         "kernel": "k_batch", "ops_per_cell": CELL_OPS,
-                         "peak_source": "measured: paco_measure_int_peak(op=0), full-rate IADD3 on all SMs"},
-            "roofline_bitparallel": {"ops_per_cell": OPS_PER_WORD_STEP / 31, "achieved": achieved_bp / 1e12,
-                                     "frac": achieved_bp / peak_ops},
-            "clocks": clocks.summary()}
-    print(json.dumps(line), flush=True)
+    rec = {"value": value, "unit": "GCUPS", "steps": steps, "warmup": warmup, "ms_per_step": sum(ms) / steps,
+           "config": {"workload": bt.name + " (seed 4)", "pairs": bt.npairs, "cells": cells,
+                      "engine": "batch graph, warp jobs", "alphabet": 4,
+                      "chunk_by_class": _chunks_by_class(ctx.get_option(P.OPT_BATCH_CHUNKS)),
+                      "l2": "flushed between timed steps"},
+           "step_ms_median": med, "step_ms_min": min(ms), "first_call_host_ms": first_ms,
+           "plain_one_pair_per_launch": plain_rec,
+           "batch_over_plain": (value / plain_rec["value"]) if plain_rec else None,
+           "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
+                        "unit": "Tops/s (int32 lane-ops, 4 per cell)", "frac": achieved / peak_ops,
+                        "traffic": _profiled_traffic("k_batch_batch4096_full.md", ["batch.cu", "bp_device.cuh"]),
+                        "duration": "whole step (column offsets + k_batch + prefixes), an upper bound on k_batch",
+                        "kernel": "k_batch", "ops_per_cell": CELL_OPS,
+                        "peak_source": "measured: paco_measure_int_peak(op=0), full-rate IADD3 on all SMs"},
+           "roofline_bitparallel": {"ops_per_cell": OPS_PER_WORD_STEP / 31, "achieved": achieved_bp / 1e12,
+                                    "frac": achieved_bp / peak_ops,
+                                    "note": "the lane-ops the bit-parallel step needs (4 per 31-row word and "
+                                            "column) over the same peak"},
+           "clocks": clocks.summary()}
     ctx.close()
+    return rec
 
 
-def run_serve_bench(args):
-    """Poisson stream of requests through paco_lcs_submit_many / paco_lcs_poll_many at
-    fractions of the saturating rate; p50/p99 latency beside throughput, and
-    the same arrival schedule served one pair per launch (FIFO) as the plain
-    comparison."""
+def run_batch_bench(args):
+    rec = batch_record(args.steps, args.warmup, plain=not args.no_plain)
+    line = {"metric": METRIC, "value": rec["value"], "unit": "GCUPS", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": rec["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic"}
+    line.update({k: v for k, v in rec.items() if k not in line})
+    print(json.dumps(line), flush=True)
+
+
+def _serve_run(P, ctx, st, arr, cells, window=16384):
+    """Submit the stream at its arrival times (every arrived request in one
+    paco_lcs_submit_many call) from a thread, poll completions, and return
+    per-request completion times (s from the start) and the wall time."""
     import threading as th
+    nreq = st.npairs
+    tickets = np.zeros(nreq, dtype=np.uint64)
+    done_t = np.full(nreq, np.nan)
+    submitted = [0]
+    t_start = time.perf_counter()
+
+    def submitter():
+        k = 0
+        while k < nreq:
+            now = time.perf_counter() - t_start
+            j = int(np.searchsorted(arr, now, side="right"))
+            if j <= k:
+                time.sleep(max(0.0, min(arr[k] - now, 0.0005)))
+                continue
+            tickets[k:j] = P.paco_lcs_submit_many(ctx, st.a_cat, st.a_off[k:j + 1], st.b_cat, st.b_off[k:j + 1])
+            submitted[0] = j
+            k = j
+    thr = th.Thread(target=submitter)
+    thr.start()
+    lo = 0  # every request before lo is done
+    while lo < nreq:
+        hi = min(submitted[0], lo + window)
+        if hi > lo:
+            idx = np.arange(lo, hi)
+            idx = idx[np.isnan(done_t[lo:hi])]
+            if idx.size:
+                status, _ = P.paco_lcs_poll_many(ctx, tickets[idx])
+                fin = idx[status != P.PACO_PENDING]
+                if fin.size:
+                    done_t[fin] = time.perf_counter() - t_start
+            while lo < hi and not np.isnan(done_t[lo]):
+                lo += 1
+        time.sleep(0.0002)
+    thr.join()
+    return done_t, float(np.nanmax(done_t) - arr[0])
+
+
+def served_record(nreq=100000, plain_prefix=5000, fracs=(0.5, 0.9, 1.0)):
+    """The serving stream through paco_lcs_submit_many / paco_lcs_poll_many at
+    fractions of the saturating rate (the batch path's rate on the same mix):
+    GCUPS, p50/p99 latency and host time per micro-batch; the plain path (one
+    pair per launch through the host-buffer entry point, FIFO) really served
+    on the first `plain_prefix` requests at 0.9 of the saturating rate."""
     import torch
     import paper_2011_01441_gb300 as P
     P.load()
+    t0 = time.perf_counter()
+    st = W.serve_stream(nreq, workers=min(16, os.cpu_count() or 1))
+    gen_s = time.perf_counter() - t0
+    cells = (np.diff(st.a_off) * np.diff(st.b_off)).astype(np.float64)
     ctx = P.Context(0, mem_budget_bytes=8 << 30)
     ctx.set_option(P.OPT_ALPHABET, 20)  # the serving mix uses symbols 0..19
-    nreq = args.requests
-    reqs = [W.serve_request(k) for k in range(nreq)]
-    cells = np.array([r.a.size * r.b.size for r in reqs], dtype=np.float64)
-    # saturating rate from the batch path on this mix
-    a_cat = np.concatenate([r.a for r in reqs]); b_cat = np.concatenate([r.b for r in reqs])
-    a_off = np.concatenate([[0], np.cumsum([r.a.size for r in reqs])]).astype(np.int64)
-    b_off = np.concatenate([[0], np.cumsum([r.b.size for r in reqs])]).astype(np.int64)
-    da, db = torch.from_numpy(a_cat).cuda(), torch.from_numpy(b_cat).cuda()
-    P.paco_lcs_batch(ctx, da, db, a_off, b_off)
+    # saturating rate: the batch path on the whole mix (autotuned once)
+    da, db = torch.from_numpy(st.a_cat).cuda(), torch.from_numpy(st.b_cat).cuda()
+    P.paco_lcs_batch(ctx, da, db, st.a_off, st.b_off)
     ctx.sync()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(); P.paco_lcs_batch(ctx, da, db, a_off, b_off); e1.record(); e1.synchronize()
+    e0.record(); P.paco_lcs_batch(ctx, da, db, st.a_off, st.b_off); e1.record(); e1.synchronize()
     sat_gcups = cells.sum() / (e0.elapsed_time(e1) * 1e-3) / 1e9
+    tuned = ctx.get_option(P.OPT_BATCH_CHUNKS)
+    ctx.set_option(P.OPT_SERVE_CHUNKS, tuned)  # the micro-batches use the batch autotuner's widths
+    del da, db
+    torch.cuda.empty_cache()
     lam_sat = sat_gcups * 1e9 / cells.mean()
     results = {}
-    for frac in (0.5, 0.9, 1.0):
+    for frac in fracs:
         lam = frac * lam_sat
         arr = W.poisson_arrivals(7, nreq, lam)
-        tickets = np.zeros(nreq, dtype=np.uint64)
-        done_t = np.full(nreq, np.nan)
-        submitted = [0]
-        t_start = time.perf_counter()
-
-        def submitter():
-            # every request whose arrival time has passed goes in one call
-            k = 0
-            while k < nreq:
-                now = time.perf_counter() - t_start
-                j = int(np.searchsorted(arr, now, side="right"))
-                if j <= k:
-                    time.sleep(max(0.0, min(arr[k] - now, 0.0005)))
-                    continue
-                tickets[k:j] = P.paco_lcs_submit_many(ctx, a_cat, a_off[k:j + 1], b_cat, b_off[k:j + 1])
-                k = j
-                submitted[0] = k
-        thr = th.Thread(target=submitter)
-        thr.start()
-        pending = np.arange(nreq)
-        while pending.size:
-            ready = pending[pending < submitted[0]]
-            if ready.size:
-                st, _ = P.paco_lcs_poll_many(ctx, tickets[ready])
-                fin = ready[st != P.PACO_PENDING]
-                if fin.size:
-                    done_t[fin] = time.perf_counter() - t_start
-                    pending = np.setdiff1d(pending, fin, assume_unique=True)
-            time.sleep(0.0002)
-        thr.join()
-        lat = np.array(done_t) - arr
-        wall = max(done_t) - arr[0]
-        results[f"{frac:.1f}"] = {"rate_per_s": lam, "gcups": cells.sum() / wall / 1e9,
-                                  "p50_ms": float(np.percentile(lat, 50) * 1e3),
-                                  "p99_ms": float(np.percentile(lat, 99) * 1e3)}
-    # plain: FIFO, one pair per launch, same arrivals at 0.9 of saturation
-    arr = W.poisson_arrivals(7, nreq, 0.9 * lam_sat)
-    service = []
-    out = torch.empty(1, dtype=torch.int32, device="cuda")
-    for r in reqs:
-        a = torch.from_numpy(r.a).cuda(); b = torch.from_numpy(r.b).cuda()
-        torch.cuda.synchronize(); t0 = time.perf_counter()
-        P.paco_lcs_length(ctx, a, b, out=out); torch.cuda.synchronize()
-        service.append(time.perf_counter() - t0)
-    fin, lat_plain = 0.0, []
-    for k in range(nreq):
-        fin = max(fin, arr[k]) + service[k]
-        lat_plain.append(fin - arr[k])
-    lat_plain = np.array(lat_plain)
-    line = {"metric": METRIC, "value": results["1.0"]["gcups"], "unit": "GCUPS", "n_gpus": 1,
-            "steps": 1, "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "u32", "data": "synthetic",
-            "config": {"workload": f"serving stream: {nreq} requests of the 100000-request mix (seed 5), lengths log-uniform [32, 65536], sigma 20, half 20%-mutated",
-                       "budget_bytes": 8 << 30, "saturating_rate_per_s": lam_sat,
-                       "batch_gcups_on_mix": sat_gcups},
-            "served": results,
-            "plain_fifo_one_pair_per_launch_at_0.9": {"gcups": cells.sum() / sum(service) / 1e9,
-                                                      "p50_ms": float(np.percentile(lat_plain, 50) * 1e3),
-                                                      "p99_ms": float(np.percentile(lat_plain, 99) * 1e3)}}
-    print(json.dumps(line), flush=True)
+        s0 = P.paco_serve_get_stats(ctx)
+        with ClockSampler(0) as clocks:
+            done_t, wall = _serve_run(P, ctx, st, arr, cells)
+        s1 = P.paco_serve_get_stats(ctx)
+        lat = done_t - arr
+        nb = max(1, s1["batches_launched"] - s0["batches_launched"])
+        results[f"{frac:.1f}"] = {
+            "rate_per_s": lam, "requests": nreq, "gcups": cells.sum() / wall / 1e9, "wall_s": wall,
+            "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+            "micro_batches": nb,
+            "host_launch_us_per_batch": (s1["host_launch_ns"] - s0["host_launch_ns"]) / nb / 1e3,
+            "host_complete_us_per_batch": (s1["host_complete_ns"] - s0["host_complete_ns"]) / nb / 1e3,
+            "clocks": clocks.summary()}
+    # plain: FIFO, one pair per launch through the host-buffer entry point, same arrivals at 0.9
+    k_plain = min(plain_prefix, nreq)
+    arr = W.poisson_arrivals(7, nreq, 0.9 * lam_sat)[:k_plain]
+    fin_t = np.zeros(k_plain)
+    t_start = time.perf_counter()
+    for k in range(k_plain):
+        now = time.perf_counter() - t_start
+        if arr[k] > now:
+            time.sleep(arr[k] - now)
+        a = st.a_cat[st.a_off[k]:st.a_off[k + 1]]
+        b = st.b_cat[st.b_off[k]:st.b_off[k + 1]]
+        P.paco_lcs_boundaries_host(ctx, a, b, want_rows=False, want_cols=False)
+        fin_t[k] = time.perf_counter() - t_start
+    lat_plain = fin_t - arr
+    plain_wall = fin_t[-1] - arr[0]
     ctx.close()
+    return {"value": results[f"{fracs[-1]:.1f}"]["gcups"], "unit": "GCUPS",
+            "config": {"workload": st.name, "requests": nreq, "budget_bytes": 8 << 30,
+                       "saturating_rate_per_s": lam_sat, "batch_gcups_on_mix": sat_gcups,
+                       "serve_chunks_by_class": _chunks_by_class(tuned), "stream_generation_s": gen_s},
+            "served": results,
+            "served_over_batch_at_1.0": results.get("1.0", {}).get("gcups", float("nan")) / sat_gcups,
+            "plain_fifo_one_pair_per_launch_at_0.9": {
+                "measured": "real: the first %d requests of the same arrival schedule, served one at a time "
+                            "(paco_lcs_boundaries_host: copy in, one launch, copy out)" % k_plain,
+                "requests": k_plain, "gcups": cells[:k_plain].sum() / plain_wall / 1e9,
+                "p50_ms": float(np.percentile(lat_plain, 50) * 1e3),
+                "p99_ms": float(np.percentile(lat_plain, 99) * 1e3)}}
+
+
+def run_serve_bench(args):
+    rec = served_record(args.requests)
+    line = {"metric": METRIC, "value": rec["value"], "unit": "GCUPS", "n_gpus": 1, "steps": 1, "warmup": 0,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic"}
+    line.update({k: v for k, v in rec.items() if k not in line})
+    print(json.dumps(line), flush=True)
 
 
 def run_recover_bench(args):
@@ -899,7 +1007,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="mutated", choices=["mutated", "small", "skinny", "batch", "serve", "recover", "schedules",
                                                                "affine", "affine_batch", "lws"])
-    ap.add_argument("--requests", type=int, default=3000, help="serving: requests taken from the stream")
+    ap.add_argument("--requests", type=int, default=100000, help="serving: requests taken from the stream")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="default workload: skip the nested small / skinny / batch / served records")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="batch: skip the one-pair-per-launch comparison")
     args = ap.parse_args()

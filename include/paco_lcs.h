@@ -82,7 +82,10 @@ const char *paco_last_error(paco_ctx *ctx);
 
 /* Wait for all work the context enqueued on `stream` (NULL: all of the
  * context's streams and the caller's last stream) and return the first
- * sticky device error (PACO_ETIMEOUT, PACO_EINVAL), clearing it. */
+ * sticky device error (PACO_ETIMEOUT, PACO_EINVAL), clearing it.  The stream
+ * argument lets a caller that keeps several streams wait for one of them
+ * without draining the others (the bounded waits of the paper's execution
+ * phase, Sec. "PACO LCS", report their timeouts here). */
 int paco_ctx_sync(paco_ctx *ctx, void *stream);
 
 /* Tunables (engine choice, chunk width, warps per CTA, wait limit ...).
@@ -118,6 +121,11 @@ enum paco_option {
                                    granules (0 = 4 for PACO, 16 for PO) */
     PACO_OPT_AFFINE_ROWS = 12,  /* affine alignment (include/paco_affine.h): rows per
                                    lane of a row band, 2, 4 or 8 (0 = 4) */
+    PACO_OPT_SERVE_CHUNKS = 13, /* serving: chunk width per size class for the
+                                   micro-batches, packed like PACO_OPT_BATCH_CHUNKS
+                                   (each 2, 4 or 8); 0 = the defaults 2, 4, 8, 8.  A
+                                   caller can pass the widths the batch autotuner
+                                   picked on a batch of the same mix */
     PACO_OPT_TEST_STALL = 100   /* tests only: make one strip (pair kernel), one
                                    band job (affine) or one block (1D problem) wait
                                    for input that never arrives (exercises the
@@ -126,13 +134,20 @@ enum paco_option {
 
 /* ---- single pair ------------------------------------------------------ */
 
-/* LCS length only.  a: device uint8[n]; b: device uint8[m]; d_len: device
- * int32[1] receiving L.  Errors: PACO_EINVAL (NULL pointer with a non-zero
+/* LCS length only: L = H[n][m] of Eq. (1), the quantity the paper's LCS
+ * section computes (Sec. "PACO LCS").  a: device uint8[n]; b: device uint8[m];
+ * d_len: device int32[1] receiving L.  Errors: PACO_EINVAL (NULL pointer with a non-zero
  * length, negative or too-large length), PACO_ENOMEM, PACO_EDEVICE. */
 int paco_lcs_length(paco_ctx *ctx, const uint8_t *a, int64_t n,
                     const uint8_t *b, int64_t m, int32_t *d_len, void *stream);
 
-/* Length plus boundaries.  d_top_in: device int32[m+1] or NULL (zeros);
+/* Length plus boundaries: the whole table of Eq. (1) with the given first
+ * row and column, returning its last row and column, i.e. one region of the
+ * paper's execution phase (Sec. "PACO LCS": a region needs only the
+ * boundaries its neighbours above and to the left hand it, and hands its own
+ * last row and column on).  The table is split across the GPU's SMs by the
+ * p-way first cut of the PACO partition (rows in balanced strips), and runs
+ * in one launch.  d_top_in: device int32[m+1] or NULL (zeros);
  * d_left_in: device int32[n+1] or NULL (zeros); d_bottom_row: device
  * int32[m+1] or NULL; d_right_col: device int32[n+1] or NULL; d_len: device
  * int32[1] or NULL.  Output buffers must not overlap inputs. */
@@ -142,7 +157,8 @@ int paco_lcs_boundaries(paco_ctx *ctx, const uint8_t *a, int64_t n,
                         int32_t *d_bottom_row, int32_t *d_right_col,
                         int32_t *d_len, void *stream);
 
-/* The same computation from HOST buffers (pageable or pinned): copies a, b
+/* The same computation (Eq. (1), Sec. "PACO LCS") from HOST buffers
+ * (pageable or pinned): copies a, b
  * (and the optional host boundaries) to the device, runs, copies the
  * requested outputs back, and returns when they are in host memory.  Any
  * output pointer may be NULL. */
@@ -191,7 +207,12 @@ int paco_lcs_boundaries_static(const uint8_t *a, int64_t n, const uint8_t *b, in
 
 /* ---- batch of independent pairs ---------------------------------------- */
 
-/* npairs independent pairs in one persistent launch.  The whole step (column
+/* npairs independent tables of Eq. (1) in one persistent launch; the balanced
+ * share of work per SM that the PACO partition gives one table (Sec. "PACO
+ * LCS") is here a longest-first order of warp jobs over many tables.  The
+ * offsets are HOST arrays because the planner needs the lengths before
+ * anything is launched (reading device offsets would cost a copy and a
+ * synchronisation per call).  The whole step (column
  * tables, the persistent warp-job kernel, the boundary prefixes) is captured
  * once into a CUDA graph per context, layout and output pointers, then
  * replayed; the chunk width is autotuned once per layout (PACO_OPT_CHUNK
@@ -216,7 +237,8 @@ int paco_lcs_batch(paco_ctx *ctx, const uint8_t *a_cat, const uint8_t *b_cat,
 
 /* ---- serving: continuous batching ------------------------------------- */
 
-/* Submit one request from HOST memory.  The library copies the strings
+/* Serving (continuous batching of tables of Eq. (1); not in the paper):
+ * submit one request from HOST memory.  The library copies the strings
  * before returning (the caller may free them).  The request is admitted to
  * the device when the context's memory budget allows, runs in a micro-batch
  * with whatever else is admitted, and is retrieved with paco_lcs_poll.

@@ -100,6 +100,24 @@ typedef struct paco_1d_task {
 int paco_plan_1d(int64_t n, int32_t p, int64_t base, paco_1d_task *out, int64_t cap, int64_t *count,
                  int32_t *phases, int64_t *temp_words);
 
+/* Shard a batch of independent pairs over `ranks` GPUs (one process per
+ * GPU).  The pairs of a batch share nothing, so the split needs no exchange
+ * of intermediate data: each rank runs its pairs with paco_lcs_batch and the
+ * results are gathered.  The split balances work the way the paper's
+ * partition balances its regions, here by size-balanced greedy assignment:
+ * pairs in decreasing order of cells n_k * m_k, each to the rank with the
+ * fewest cells so far (ties to the lowest rank; equal pairs keep index
+ * order).  Every rank's total then exceeds the smallest total by at most
+ * the largest single pair.
+ *   a_off, b_off : int64[npairs+1] offsets (pair k is n_k = a_off[k+1] -
+ *                  a_off[k] by m_k = b_off[k+1] - b_off[k]), host memory
+ *   owner        : int32[npairs] out: the rank of each pair
+ *   rank_cells   : int64[ranks] out (may be NULL): cells per rank
+ * Returns 0, or -1 for npairs < 0, ranks < 1, NULL arrays or decreasing
+ * offsets. */
+int paco_plan_shard(const int64_t *a_off, const int64_t *b_off, int64_t npairs, int32_t ranks, int32_t *owner,
+                    int64_t *rank_cells);
+
 #ifdef __cplusplus
 }
 #endif

@@ -40,6 +40,7 @@ OPT_WORDS_PER_LANE = 9
 OPT_TILES = 10
 OPT_TILE_BASE = 11
 OPT_AFFINE_ROWS = 12
+OPT_SERVE_CHUNKS = 13
 OPT_TEST_STALL = 100
 
 _lib = None
@@ -123,6 +124,7 @@ def load():
         "paco_affine_batch": ([P, P, P, P, P, I32, ctypes.POINTER(PacoAffineScores), P, P], INT),
         "paco_lws": ([P, I64, I32, ctypes.POINTER(PacoLwsWeight), P, P], INT),
         "paco_plan_1d": ([I64, I32, I64, P, I64, ctypes.POINTER(I64), ctypes.POINTER(I32), ctypes.POINTER(I64)], INT),
+        "paco_plan_shard": ([P, P, I64, I32, P, P], INT),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)

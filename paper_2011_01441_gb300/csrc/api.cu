@@ -186,6 +186,16 @@ int paco_ctx_set_option(paco_ctx *ctx, int option, int64_t value) {
             if (!(value == 0 || value == 2 || value == 4 || value == 8)) return PACO_EINVAL;
             ctx->opt_affine_rows = (int)value;
             return PACO_OK;
+        case PACO_OPT_SERVE_CHUNKS:
+            if (value != 0) {
+                for (int k = 0; k < 4; ++k) {
+                    const int64_t c = (value >> (4 * k)) & 15;
+                    if (!(c == 2 || c == 4 || c == 8)) return PACO_EINVAL;
+                }
+                if (value >> 16) return PACO_EINVAL;
+            }
+            ctx->opt_serve_chunks = (int)value;
+            return PACO_OK;
         case PACO_OPT_TEST_STALL:
             if (value < -1 || value > 0x7fffffff) return PACO_EINVAL;
             ctx->test_stall = (int)value;
@@ -210,6 +220,7 @@ int paco_ctx_get_option(paco_ctx *ctx, int option, int64_t *value) {
         case PACO_OPT_TILE_BASE: *value = ctx->opt_tile_base; return PACO_OK;
         case PACO_OPT_BATCH_CHUNKS: *value = ctx->last_batch_chunk; return PACO_OK;
         case PACO_OPT_AFFINE_ROWS: *value = ctx->opt_affine_rows; return PACO_OK;
+        case PACO_OPT_SERVE_CHUNKS: *value = ctx->opt_serve_chunks; return PACO_OK;
         case PACO_OPT_TEST_STALL: *value = ctx->test_stall; return PACO_OK;
         default: return PACO_EINVAL;
     }

@@ -797,7 +797,10 @@ int run_batch(paco_ctx *ctx, BatchState *B, const uint8_t *a_cat, const int64_t 
     if (force_chunk) {
         cls = {force_chunk, force_chunk, force_chunk, force_chunk};
     } else if (B != ctx->batch) {
-        cls = {2, 4, 8, 8};  // serving micro-batches: untuned defaults by size class
+        // serving micro-batches: the caller's widths per size class, else defaults
+        const int sc = ctx->opt_serve_chunks;
+        cls = sc ? std::array<int, 4>{sc & 15, (sc >> 4) & 15, (sc >> 8) & 15, (sc >> 12) & 15}
+                 : std::array<int, 4>{2, 4, 8, 8};
     } else {
         auto it = B->tuned.find(key);
         if (it != B->tuned.end()) {

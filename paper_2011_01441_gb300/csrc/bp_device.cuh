@@ -152,6 +152,12 @@ static __device__ __forceinline__ int ld_acquire_shared(uint32_t addr) {
 static __device__ __forceinline__ void st_release_shared(uint32_t addr, int v) {
     asm volatile("st.release.cta.shared.s32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
 }
+// An acquire load that only some iterations take: with p false the register
+// keeps its value (predicated, no branch).
+static __device__ __forceinline__ void ld_acquire_shared_if(bool p, uint32_t addr, int &v) {
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %1, 0;\n\t@q ld.acquire.cta.shared.s32 %0, [%2];\n\t}"
+                 : "+r"(v) : "r"((uint32_t)p), "r"(addr) : "memory");
+}
 // The same, predicated (no branch around a one-lane store).
 static __device__ __forceinline__ void st_release_shared_if(bool p, uint32_t addr, int v) {
     asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %0, 0;\n\t@q st.release.cta.shared.s32 [%1], %2;\n\t}"

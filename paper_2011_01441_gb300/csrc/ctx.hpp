@@ -46,6 +46,7 @@ struct paco_ctx {
     int opt_tiles = 0;            // single pair: 0 = strip pipeline, 1..3 = tile schedule (PACO, PA, PO)
     int64_t opt_tile_base = 0;    // tile schedules: smallest tile side in granules (0 = per schedule)
     int opt_affine_rows = 0;      // affine alignment: rows per lane, 4 or 8 (0 = 4)
+    int opt_serve_chunks = 0;     // serving micro-batches: packed chunk width per size class (0 = defaults)
     int test_stall = -1;
     int opt_alphabet = 256;
     long long wait_limit_ns = 2000000000LL;

@@ -460,12 +460,18 @@ __global__ void __launch_bounds__(256, 1) k_pair_bp(const PairArgs P) {
         uint32_t Mlow[C];       // two words: the lower word's match words for this step
         bool ok = true;
         int cons_seen = 0;      // downstream consumer's progress word, last read
+        int cols_seen = 0;      // the producer's column count, last read
         uint32_t steps_in = 0;  // set bits of the input carry words: horizontal steps along row wrow0
         const bool out_shared = (w + 1 < W) || last_strip;
         uint64_t *dst_row = P.hbuf + (size_t)(s + 1) * P.hstride;
         // the input carry word of the next 32-column word, read kPrefetch steps
         // before it is needed (so its load never stalls the column chain)
         constexpr int kPrefetch = K >= 8 ? K - 4 : 0;
+        // the producer's count for the next word (acquire), then the vote on
+        // the next word's needs, late in the word but a shared load's latency
+        // after the loads they test
+        constexpr int kAcquireStep = K >= 8 ? K - 3 : 1;
+        constexpr int kVoteStep = K >= 8 ? K - 2 : 2;
         auto in_slot = [&](int q) { return in_s + (((uint32_t)q & in_mask) << 3); };
         uint64_t in_next = nwords > 0 ? lds_u64(in_slot(0)) : 0ull;
         {   // the first word's offsets and match words (later words: carried over)
@@ -484,101 +490,117 @@ __global__ void __launch_bounds__(256, 1) k_pair_bp(const PairArgs P) {
             }
             offs_at<C>(cb0 + (uint32_t)(C * 4), onext);
         }
-        for (int u = 0; u < nouter; ++u) {
-            // once per kCheckEvery words, for all of them: the column ring is
-            // filled far enough, and the consumer of this warp's output words
-            // (the next warp, or the producer for the bottom row) has freed the
-            // ring slots they go to.  Conditions are votes, so branches are
-            // warp-uniform.
-            if ((u & (kCheckEvery - 1)) == 0) {
-                const int need_c = min(u + kCheckEvery + 1, nvwords);
-                if (__any_sync(kFull, ld_acquire_shared(prod_cols) < need_c) &&
-                    !wait_cols(prod_cols, need_c, P.err, P.wait_limit_ns)) {
+        // Word u needs: the column ring filled up to word u + 1 (the words its
+        // lanes read; the producer's count is read with acquire, and the reads
+        // of the ring follow it), its input carry word tagged u + 1 (warp 0's
+        // from the producer, the others' from the warp above), and, when its
+        // lane 31 flushes into a shared ring, that slot read by the consumer
+        // (the next warp, or the producer for the bottom row).  The fast loop
+        // tests the next word's needs by one vote in the middle of the current
+        // word, so the branch at the word boundary finds its predicate ready,
+        // and it leaves before the first word that lacks something.  The waits
+        // (function calls) sit in the slow path outside it.
+        int u = 0;
+        for (;;) {
+            if (u >= nouter) break;
+            {   // the slow path: wait (bounded) for what word u lacks
+                const int need_c = min(u + 2, nvwords);
+                const int wq_u = ((u * K + kFlushStep - kLag) * C) >> 5;
+                const int need_out = out_shared ? min(wq_u, nwords - 1) - kRing + 1 : 0;
+                if (!wait_cols(prod_cols, need_c, P.err, P.wait_limit_ns)) {
                     ok = false;
                     break;
                 }
-                if (out_shared) {
-                    // the last word flushed in these kCheckEvery words
-                    const int wq_hi = (((u + kCheckEvery - 1) * K + kFlushStep - kLag) * C) >> 5;
-                    const int need = min(wq_hi, nwords - 1) - kRing + 1;
-                    if (need > cons_seen) {
-                        if (!__all_sync(kFull, wait_consumed(cons + w + 1, need, P.err, P.wait_limit_ns))) {
-                            ok = false;
-                            break;
-                        }
-                        cons_seen = cons[w + 1];
-                    }
-                }
-            }
-            // the input carry word u: warp 0's from the producer, others' from the warp above
-            uint32_t srcw = 0;
-            if (u < nwords) {
-                uint64_t v = in_next;
-                if (!__all_sync(kFull, (uint32_t)(v >> 32) == (uint32_t)(u + 1))) {
-                    v = wait_tagged(reinterpret_cast<const uint64_t *>(smem + (in_slot(u) - sbase)), (uint32_t)(u + 1),
-                                    P.err, P.wait_limit_ns);
-                    if (!__all_sync(kFull, (uint32_t)(v >> 32) == (uint32_t)(u + 1))) {
+                cols_seen = ld_acquire_shared(prod_cols);
+                if (u < nwords && !__all_sync(kFull, (uint32_t)(in_next >> 32) == (uint32_t)(u + 1))) {
+                    in_next = wait_tagged(reinterpret_cast<const uint64_t *>(smem + (in_slot(u) - sbase)),
+                                          (uint32_t)(u + 1), P.err, P.wait_limit_ns);
+                    if (!__all_sync(kFull, (uint32_t)(in_next >> 32) == (uint32_t)(u + 1))) {
                         ok = false;
                         break;
                     }
                 }
-                srcw = (uint32_t)v;
-                steps_in += __popc(srcw);
+                if (need_out > cons_seen) {
+                    if (!__all_sync(kFull, wait_consumed(cons + w + 1, need_out, P.err, P.wait_limit_ns))) {
+                        ok = false;
+                        break;
+                    }
+                    cons_seen = cons[w + 1];
+                }
             }
-            st_release_shared_if(lane == 0 && (u & (kCheckEvery - 1)) == kCheckEvery - 1, cons_s + 4u * (uint32_t)w,
-                                 u + 1);
-            const int ubase = u * K;
-            // this lane's column of step 0 (upper word) and its place in the ring
-            const int c0 = u * 32 - kSk * C * lane;
-            const uint32_t cbase = col_ring + (uint32_t)(((c0 >> 5) & (R - 1)) * 128) + (uint32_t)((c0 & 31) * 4);
-            if (lane == 0) sr[0] = srcw;
-            // Software pipeline: offsets two steps ahead, match words one step
-            // ahead, the carry hand-off after the step's columns (its result is
-            // used three steps later), so a warp issuing in order never waits on
-            // a shared load or a shuffle before a column.  Columns outside
-            // [0, S) read the zero row: no per-lane activity tests.
+            bool stop = false;  // the next word lacks something
+#pragma unroll 2
+            for (; u < nouter;) {
+                // the input carry word u (its tag was checked)
+                const uint32_t srcw = u < nwords ? (uint32_t)in_next : 0u;
+                steps_in += __popc(srcw);
+                st_release_shared_if(lane == 0 && (u & (kCheckEvery - 1)) == kCheckEvery - 1, cons_s + 4u * (uint32_t)w,
+                                     u + 1);
+                const int ubase = u * K;
+                // this lane's column of step 0 (upper word) and its place in the ring
+                const int c0 = u * 32 - kSk * C * lane;
+                const uint32_t cbase = col_ring + (uint32_t)(((c0 >> 5) & (R - 1)) * 128) + (uint32_t)((c0 & 31) * 4);
+                if (lane == 0) sr[0] = srcw;
+                // Software pipeline: offsets two steps ahead, match words one step
+                // ahead, the carry hand-off after the step's columns (its result is
+                // used three steps later), so a warp issuing in order never waits on
+                // a shared load or a shuffle before a column.  Columns outside
+                // [0, S) read the zero row: no per-lane activity tests.
 #pragma unroll
-            for (int i = 0; i < K; ++i) {
-                uint32_t onext2[C], Mnext[C], Mlow_next[C];
-                offs_at<C>(cbase + (uint32_t)((i + 2) * C * 4), onext2);
-                match_words<C>(pm_lane0, onext, Mnext);
-                if constexpr (WPL == 2) match_words<C>(pm_lane1, oprev, Mlow_next);
-                if (i == kPrefetch) in_next = (u + 1 < nwords) ? lds_u64(in_slot(u + 1)) : 0ull;
-                if (lane != 0) sr[0] = cin_cur << (32 - C);
-                if constexpr (WPL == 2) {
-                    sr[1] = cw[0] << (32 - C);  // the upper word's carries of the step before
+                for (int i = 0; i < K; ++i) {
+                    uint32_t onext2[C], Mnext[C], Mlow_next[C];
+                    offs_at<C>(cbase + (uint32_t)((i + 2) * C * 4), onext2);
+                    match_words<C>(pm_lane0, onext, Mnext);
+                    if constexpr (WPL == 2) match_words<C>(pm_lane1, oprev, Mlow_next);
+                    if (i == kPrefetch) in_next = lds_u64(in_slot(u + 1));  // any slot is readable
+                    if (i == kAcquireStep)  // the count the next word's reads follow, once per kCheckEvery words
+                        ld_acquire_shared_if(((u + 1) & (kCheckEvery - 1)) == 0, prod_cols, cols_seen);
+                    if (i == kVoteStep) {  // the next word's needs
+                        const int v1 = u + 1;
+                        const int need_c = min(v1 + 2, nvwords);
+                        const int wq_v = ((v1 * K + kFlushStep - kLag) * C) >> 5;
+                        const int need_out = out_shared ? min(wq_v, nwords - 1) - kRing + 1 : 0;
+                        const bool stale = v1 < nwords && (uint32_t)(in_next >> 32) != (uint32_t)(v1 + 1);
+                        stop = __any_sync(kFull, cols_seen < need_c || stale || need_out > cons_seen);
+                    }
+                    if (lane != 0) sr[0] = cin_cur << (32 - C);
+                    if constexpr (WPL == 2) {
+                        sr[1] = cw[0] << (32 - C);  // the upper word's carries of the step before
+#pragma unroll
+                        for (int jj = 0; jj < C; ++jj) {
+                            column31c(Sv[0], Yv[0], sr[0], cw[0], Mcur[jj]);
+                            column31c(Sv[1], Yv[1], sr[1], cw[1], Mlow[jj]);
+                        }
+                    } else {
+#pragma unroll
+                        for (int jj = 0; jj < C; ++jj) column31c(Sv[0], Yv[0], sr[0], cw[0], Mcur[jj]);
+                    }
+                    const uint32_t recv = __shfl_up_sync(kFull, cw[WPL - 1], 1);
+                    cin_cur = cin_nxt;
+                    cin_nxt = cin_n2;
+                    cin_n2 = recv;
 #pragma unroll
                     for (int jj = 0; jj < C; ++jj) {
-                        column31c(Sv[0], Yv[0], sr[0], cw[0], Mcur[jj]);
-                        column31c(Sv[1], Yv[1], sr[1], cw[1], Mlow[jj]);
+                        Mcur[jj] = Mnext[jj];
+                        if constexpr (WPL == 2) {
+                            Mlow[jj] = Mlow_next[jj];
+                            oprev[jj] = onext[jj];
+                        }
+                        onext[jj] = onext2[jj];
                     }
-                } else {
-#pragma unroll
-                    for (int jj = 0; jj < C; ++jj) column31c(Sv[0], Yv[0], sr[0], cw[0], Mcur[jj]);
-                }
-                const uint32_t recv = __shfl_up_sync(kFull, cw[WPL - 1], 1);
-                cin_cur = cin_nxt;
-                cin_nxt = cin_n2;
-                cin_n2 = recv;
-#pragma unroll
-                for (int jj = 0; jj < C; ++jj) {
-                    Mcur[jj] = Mnext[jj];
-                    if constexpr (WPL == 2) {
-                        Mlow[jj] = Mlow_next[jj];
-                        oprev[jj] = onext[jj];
+                    if (i == kFlushStep) {  // lane 31 completes word wq: predicated stores, no branch
+                        const int wq = ((ubase + i - kLag) * C) >> 5;
+                        const bool fl = lane == 31 && wq >= 0 && wq < nwords;
+                        const uint64_t word = ((uint64_t)(uint32_t)(wq + 1) << 32) | cw[WPL - 1];
+                        // to the next warp or the producer (the slot was checked free) ...
+                        sts_u64_if(fl && out_shared, ring_out_s + (uint32_t)((wq & (kRing - 1)) * 8), word);
+                        // ... or to the next strip, tagged with the launch epoch
+                        st_relaxed_u64_if(fl && !out_shared, dst_row + (fl ? wq : 0),
+                                          ((uint64_t)P.epoch << 32) | cw[WPL - 1]);
                     }
-                    onext[jj] = onext2[jj];
-                }
-                if (i == kFlushStep) {  // lane 31 completes word wq: predicated stores, no branch
-                    const int wq = ((ubase + i - kLag) * C) >> 5;
-                    const bool fl = lane == 31 && wq >= 0 && wq < nwords;
-                    const uint64_t word = ((uint64_t)(uint32_t)(wq + 1) << 32) | cw[WPL - 1];
-                    // to the next warp or the producer (the slot was checked free) ...
-                    sts_u64_if(fl && out_shared, ring_out_s + (uint32_t)((wq & (kRing - 1)) * 8), word);
-                    // ... or to the next strip, tagged with the launch epoch
-                    st_relaxed_u64_if(fl && !out_shared, dst_row + (fl ? wq : 0),
-                                      ((uint64_t)P.epoch << 32) | cw[WPL - 1]);
-                }
+            }
+            ++u;
+            if (stop) break;
             }
         }
         if (lane == 0) st_release_shared(cons_s + 4u * (uint32_t)w, nouter);

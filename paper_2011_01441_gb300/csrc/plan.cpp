@@ -230,6 +230,35 @@ bool plan_pair(int64_t n, int64_t m, int sms, const PairPlanOptions &o, PairPlan
     return true;
 }
 
+bool plan_shard(const int64_t *a_off, const int64_t *b_off, int64_t npairs, int ranks,
+                std::vector<int32_t> &owner, std::vector<int64_t> &rank_cells) {
+    if (npairs < 0 || ranks < 1 || (npairs > 0 && (!a_off || !b_off))) return false;
+    std::vector<int64_t> cells((size_t)npairs);
+    for (int64_t k = 0; k < npairs; ++k) {
+        const int64_t n = a_off[k + 1] - a_off[k], m = b_off[k + 1] - b_off[k];
+        if (n < 0 || m < 0) return false;
+        cells[(size_t)k] = n * m;
+    }
+    std::vector<int64_t> order((size_t)npairs);
+    for (int64_t k = 0; k < npairs; ++k) order[(size_t)k] = k;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int64_t x, int64_t y) { return cells[(size_t)x] > cells[(size_t)y]; });
+    owner.assign((size_t)npairs, 0);
+    rank_cells.assign((size_t)ranks, 0);
+    // least-loaded rank first; ties to the lowest rank
+    using Item = std::pair<int64_t, int32_t>;
+    std::priority_queue<Item, std::vector<Item>, std::greater<Item>> heap;
+    for (int32_t r = 0; r < ranks; ++r) heap.push({0, r});
+    for (int64_t k : order) {
+        const Item it = heap.top();
+        heap.pop();
+        owner[(size_t)k] = it.second;
+        rank_cells[(size_t)it.second] += cells[(size_t)k];
+        heap.push({it.first + cells[(size_t)k], it.second});
+    }
+    return true;
+}
+
 namespace {
 
 struct GTile {  // a tile in granules

@@ -67,6 +67,12 @@ struct PairPlanOptions {
 
 bool plan_pair(int64_t n, int64_t m, int sms, const PairPlanOptions &o, PairPlan &out);
 
+// Size-balanced greedy assignment of independent pairs to `ranks`: largest
+// cells first, each to the least-loaded rank (ties: lowest rank).  Returns
+// false on bad arguments.
+bool plan_shard(const int64_t *a_off, const int64_t *b_off, int64_t npairs, int ranks,
+                std::vector<int32_t> &owner, std::vector<int64_t> &rank_cells);
+
 // Balanced integer split of `total` units into `parts` (first total%parts get one more).
 std::vector<int64_t> balanced_split(int64_t total, int64_t parts);
 

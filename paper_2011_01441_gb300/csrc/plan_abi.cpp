@@ -97,4 +97,16 @@ int paco_plan_tiles(int64_t n, int64_t m, int32_t p, int32_t kind, int64_t base,
     return 0;
 }
 
+int paco_plan_shard(const int64_t *a_off, const int64_t *b_off, int64_t npairs, int32_t ranks, int32_t *owner,
+                    int64_t *rank_cells) {
+    if (npairs > 0 && !owner) return -1;
+    std::vector<int32_t> own;
+    std::vector<int64_t> rc;
+    if (!paco::plan_shard(a_off, b_off, npairs, ranks, own, rc)) return -1;
+    for (int64_t k = 0; k < npairs; ++k) owner[k] = own[(size_t)k];
+    if (rank_cells)
+        for (int32_t r = 0; r < ranks; ++r) rank_cells[r] = rc[(size_t)r];
+    return 0;
+}
+
 }  // extern "C"

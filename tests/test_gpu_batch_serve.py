@@ -151,16 +151,30 @@ def test_batch_empty_and_all_degenerate(ctx):
 
 def test_batch_full_workload_4096_pairs(ctx):
     """The 4096-pair workload (lengths log-uniform in [64, 8192], alphabet 4,
-    15% mutation) in the configuration the benchmark times: every pair's
-    length against the oracle (oracle spread over all host cores)."""
+    15% mutation) in the configuration the benchmark times (alphabet declared,
+    lengths only, graph replay), then with both boundaries: every pair's
+    length, last row and last column against the oracle (oracle spread over
+    all host cores)."""
     import torch
     bt = W.batch_pairs()
     da = torch.from_numpy(bt.a_cat).cuda()
     db = torch.from_numpy(bt.b_cat).cuda()
-    L = P.paco_lcs_batch(ctx, da, db, bt.a_off, bt.b_off)
-    ctx.sync()
-    Lo, *_ = oracle.lcs_batch(bt.a_cat, bt.a_off, bt.b_cat, bt.b_off, boundaries=False)
-    assert np.array_equal(L.cpu().numpy(), Lo)
+    Lo, rows_o, row_off, cols_o, col_off = oracle.lcs_batch(bt.a_cat, bt.a_off, bt.b_cat, bt.b_off)
+    ctx.set_option(P.OPT_ALPHABET, 4)
+    try:
+        L = P.paco_lcs_batch(ctx, da, db, bt.a_off, bt.b_off)
+        ctx.sync()
+        assert np.array_equal(L.cpu().numpy(), Lo)
+        rows = torch.empty(int(row_off[-1]), dtype=torch.int32, device="cuda")
+        cols = torch.empty(int(col_off[-1]), dtype=torch.int32, device="cuda")
+        L2 = P.paco_lcs_batch(ctx, da, db, bt.a_off, bt.b_off, rows_cat=rows, h_row_off=row_off[:-1],
+                              cols_cat=cols, h_col_off=col_off[:-1])
+        ctx.sync()
+    finally:
+        ctx.set_option(P.OPT_ALPHABET, 256)
+    assert np.array_equal(L2.cpu().numpy(), Lo)
+    assert np.array_equal(rows.cpu().numpy(), rows_o)
+    assert np.array_equal(cols.cpu().numpy(), cols_o)
 
 
 # ---------------------------------------------------------------- serving
