@@ -363,18 +363,17 @@ def _pair_timing(P, ctx, pair, steps, warmup, dev, stream, flush, rank_sync=Fals
 
 def _pair_model(plan, kmed, clk):
     """The critical-path model of the strip pipeline: every lane streams all S
-    columns, and lane k starts skew x C columns after lane k-1 (skew 3 chunks
-    with one word per lane, 4 with two), at the column chain's latency."""
+    columns, and lane k starts skew x C columns after lane k-1 (skew 3
+    chunks), at the column chain's latency."""
     sm_hz = (clk["sm_mhz"] if clk else 2070.0) * 1e6
     wpl = plan.get("words_per_lane", 1)
     lanes = (plan["L"] + 31 * wpl - 1) // (31 * wpl)
-    cp_steps = plan["S"] + (3 if wpl == 1 else 4) * plan["chunk"] * lanes
+    cp_steps = plan["S"] + 3 * plan["chunk"] * lanes
     cp_ms = cp_steps * CHAIN_CYCLES_PER_COLUMN / sm_hz * 1e3
     return {"bound": "dependency chain", "model_ms": cp_ms, "measured_ms": kmed, "frac": cp_ms / kmed,
             "column_steps": cp_steps, "cycles_per_column": CHAIN_CYCLES_PER_COLUMN,
             "measured_cycles_per_column_step": kmed * 1e-3 * sm_hz / cp_steps,
-            "note": "one lane streams all S columns; lanes trail by 3 (one word per lane) or 4 (two words) "
-                    "chunks each"}
+            "note": "one lane streams all S columns; lanes trail by 3 chunks each"}
 
 
 def pair_record(P, ctx, name, steps, warmup, dev, stream, flush, peak_ops, sms):
@@ -593,7 +592,7 @@ def run_batch_bench(args):
     print(json.dumps(line), flush=True)
 
 
-def _serve_run(P, ctx, st, arr, cells, window=16384):
+def _serve_run(P, ctx, st, arr, cells, window=4096):
     """Submit the stream at its arrival times (every arrived request in one
     paco_lcs_submit_many call) from a thread, poll completions, and return
     per-request completion times (s from the start) and the wall time."""
@@ -630,7 +629,7 @@ def _serve_run(P, ctx, st, arr, cells, window=16384):
                     done_t[fin] = time.perf_counter() - t_start
             while lo < hi and not np.isnan(done_t[lo]):
                 lo += 1
-        time.sleep(0.0002)
+        time.sleep(0.0003)
     thr.join()
     return done_t, float(np.nanmax(done_t) - arr[0])
 
@@ -678,6 +677,8 @@ def served_record(nreq=100000, plain_prefix=5000, fracs=(0.5, 0.9, 1.0)):
             "micro_batches": nb,
             "host_launch_us_per_batch": (s1["host_launch_ns"] - s0["host_launch_ns"]) / nb / 1e3,
             "host_complete_us_per_batch": (s1["host_complete_ns"] - s0["host_complete_ns"]) / nb / 1e3,
+            "host_stage_us_per_batch": (s1["host_stage_ns"] - s0["host_stage_ns"]) / nb / 1e3,
+            "host_batch_us_per_batch": (s1["host_batch_ns"] - s0["host_batch_ns"]) / nb / 1e3,
             "clocks": clocks.summary()}
     # plain: FIFO, one pair per launch through the host-buffer entry point, same arrivals at 0.9
     k_plain = min(plain_prefix, nreq)

@@ -285,6 +285,8 @@ typedef struct paco_serve_stats {
     uint64_t queued_now, inflight_now, batches_launched;
     uint64_t bytes_in_use, bytes_budget;
     uint64_t host_launch_ns, host_complete_ns;
+    uint64_t host_stage_ns, host_batch_ns;  /* parts of host_launch_ns: staging the strings, and
+                                               planning and enqueueing the batch */
 } paco_serve_stats;
 int paco_serve_get_stats(paco_ctx *ctx, paco_serve_stats *out);
 

@@ -82,7 +82,8 @@ class PacoLwsWeight(ctypes.Structure):
 class PacoServeStats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_uint64) for k in
                 ("submitted", "completed", "cells_done", "queued_now", "inflight_now",
-                 "batches_launched", "bytes_in_use", "bytes_budget", "host_launch_ns", "host_complete_ns")]
+                 "batches_launched", "bytes_in_use", "bytes_budget", "host_launch_ns", "host_complete_ns",
+                 "host_stage_ns", "host_batch_ns")]
 
 
 def load():

@@ -8,13 +8,13 @@
 // computes column t - i.  The R cells a lane computes in one step are then
 // independent of each other; each takes (H, F, symbol) of the row above from
 // the previous step: from its own registers, from the lane above by one
-// shuffle, or, for the band's first row, from a 16-column staging buffer in
+// shuffle, or, for the band's first row, from a 32-column staging buffer in
 // shared memory.  The band's last row is parked in shared memory by its
-// lane, one predicated store per step, and published once per 16 steps as
+// lane, one predicated store per step, and published once per 32 steps as
 // one 64-bit word per column in global memory: H, H - F and the launch's
 // tag, written and read as single 64-bit accesses, so the band below can
 // tell a published word from a stale one without fences or flags.  The band below loads the words of the next
-// 16 columns one chunk ahead and checks their tags when it stages them.
+// 32 columns one chunk ahead and checks their tags when it stages them.
 // Bands are jobs taken from an atomic ticket in an order in which every band
 // comes after the band above it, so a band only ever waits for a running one.
 #include "../../include/paco_affine.h"
@@ -37,7 +37,7 @@ namespace {
 // +-2^29 by the argument checks) with room to subtract scores for the few
 // hundred steps a row runs before its first column.
 constexpr int kNeg = -(1 << 30);
-constexpr int kAffChunk = 16;           // columns per staging chunk of a band's first row
+constexpr int kAffChunk = 32;           // columns per staging chunk of a band's first row (one per lane)
 constexpr int kAffWarps = 4;            // warps per CTA (independent job takers)
 constexpr int kNoSym = -1;              // column symbol outside [1, m]: never equal
 constexpr int kDeadRow = 256;           // row symbol of a row past the band: never equal

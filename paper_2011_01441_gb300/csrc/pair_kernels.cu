@@ -48,13 +48,14 @@ namespace {
 
 using namespace dev;
 
-// Lane skew in chunks: with one word per lane, lane k works on chunk t - 3k
-// at step t; with two words (the lower word one chunk behind the upper, fed
-// by its carries in registers) lane k's upper word works on chunk t - 4k.
-// Either way the carry word a lane receives from the lane above (one
-// __shfl_up_sync after each step's columns) was sent three steps before it
-// is needed, which keeps the shuffle's latency off the column chain.
-template <int WPL> __host__ __device__ constexpr int lane_skew() { return WPL == 1 ? 3 : 4; }
+// Lane skew in chunks: lane k works on chunk t - 3k at step t (with two
+// words per lane, the lower word one chunk behind the upper, fed by its
+// carries in registers).  The carry word a lane receives from the lane above
+// (one __shfl_up_sync after each step's columns) was sent kSk - WPL + 1
+// steps before it is needed: three with one word per lane, two with two
+// words (whose lower word's columns already separate the shuffle from its
+// use), which keeps the shuffle's latency off the column chain.
+template <int WPL> __host__ __device__ constexpr int lane_skew() { return 3; }
 // Chunks the last word of lane 31 trails the first word of lane 0.
 template <int WPL> __host__ __device__ constexpr int lane_lag() { return lane_skew<WPL>() * 31 + (WPL - 1); }
 // Warp 0's input carry words pass through a ring of tagged 64-bit words
@@ -73,7 +74,7 @@ constexpr uint32_t kZeroRow = (uint32_t)kMaxSigma * 128u;
 // Column-word lag of the oldest word a warp still reads behind the word its
 // lane 0 is on (the lower word reuses the upper word's offsets).
 __host__ __device__ constexpr int col_lag_words(int C, int WPL) {
-    return ((WPL == 1 ? 3 : 4) * 31 * C + (WPL - 1) * C + 31) / 32 + 1;
+    return (3 * 31 * C + (WPL - 1) * C + 31) / 32 + 1;
 }
 // Column-offset ring slots (a power of two) for C, W compute warps and WPL
 // words per lane: the lag of the last warp behind the first, the in-warp lag,
@@ -452,8 +453,11 @@ __global__ void __launch_bounds__(256, 1) k_pair_bp(const PairArgs P) {
             cw[x] = 0;
             sr[x] = 0;
         }
-        // the lane above's carry words: for this step, and the two after it
-        uint32_t cin_cur = 0, cin_nxt = 0, cin_n2 = 0;
+        // the lane above's carry words: for this step and the ones after it
+        constexpr int kQ = kSk - WPL + 1;
+        uint32_t cinq[kQ];
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) cinq[q] = 0;
         uint32_t Mcur[C];       // the upper word's match words for this step
         uint32_t onext[C];      // the next step's column offsets
         uint32_t oprev[C];      // two words: this step's offsets, for the lower word next step
@@ -563,7 +567,7 @@ __global__ void __launch_bounds__(256, 1) k_pair_bp(const PairArgs P) {
                         const bool stale = v1 < nwords && (uint32_t)(in_next >> 32) != (uint32_t)(v1 + 1);
                         stop = __any_sync(kFull, cols_seen < need_c || stale || need_out > cons_seen);
                     }
-                    if (lane != 0) sr[0] = cin_cur << (32 - C);
+                    if (lane != 0) sr[0] = cinq[0] << (32 - C);
                     if constexpr (WPL == 2) {
                         sr[1] = cw[0] << (32 - C);  // the upper word's carries of the step before
 #pragma unroll
@@ -576,9 +580,9 @@ __global__ void __launch_bounds__(256, 1) k_pair_bp(const PairArgs P) {
                         for (int jj = 0; jj < C; ++jj) column31c(Sv[0], Yv[0], sr[0], cw[0], Mcur[jj]);
                     }
                     const uint32_t recv = __shfl_up_sync(kFull, cw[WPL - 1], 1);
-                    cin_cur = cin_nxt;
-                    cin_nxt = cin_n2;
-                    cin_n2 = recv;
+#pragma unroll
+                    for (int q = 0; q + 1 < kQ; ++q) cinq[q] = cinq[q + 1];
+                    cinq[kQ - 1] = recv;
 #pragma unroll
                     for (int jj = 0; jj < C; ++jj) {
                         Mcur[jj] = Mnext[jj];

@@ -178,14 +178,14 @@ bool plan_pair(int64_t n, int64_t m, int sms, const PairPlanOptions &o, PairPlan
     out.C = o.chunk ? o.chunk : ((out.S >= 64) ? 2 : 4);
     // words per lane: each lane streams all S columns after a fill of
     // (lanes x skew x C) column steps; two words per lane halve the lanes and
-    // take a longer skew and step (skew 4 chunks against 3; the step's time
-    // ratio is measured on GB300).  Pick the smaller modelled time.
+    // take a longer step (the same skew of 3 chunks; the step's time ratio is
+    // measured on GB300).  Pick the smaller modelled time.
     if (o.wpl == 1 || o.wpl == 2) {
         out.wpl = o.wpl;
     } else {
         auto cost = [&](int wpl) {
             const double lanes = (double)((out.L + kPlanLaneRows * wpl - 1) / (kPlanLaneRows * wpl));
-            const double skew = wpl == 1 ? 3.0 : 4.0, step = wpl == 1 ? 1.0 : 1.18;
+            const double skew = 3.0, step = wpl == 1 ? 1.0 : 1.18;
             return step * ((double)out.S + lanes * skew * out.C);
         };
         out.wpl = cost(2) < cost(1) ? 2 : 1;

@@ -1,11 +1,12 @@
 // Serving: continuous batching of LCS requests under a device-memory budget.
 //
 // paco_lcs_submit copies a request into the host queue and returns a ticket.
-// A worker thread admits queued requests while the budget allows, packs the
-// admitted ones into a micro-batch and launches it (the batch engine, one
-// persistent launch) on one of kStreams streams, so micro-batches overlap on
-// the device; when a micro-batch's completion event fires its results are
-// copied into the requests and their budget is released.  paco_lcs_poll
+// One worker thread per stream slot (kStreams of them) admits queued
+// requests while the budget allows, packs them into a micro-batch and
+// launches it (the batch engine, one persistent launch) on its slot's
+// stream, so micro-batches overlap on the device and their host preparation
+// runs in parallel; when a micro-batch's completion event fires its results
+// are copied into the requests and their budget is released.  paco_lcs_poll
 // returns PACO_PENDING until then.
 #include "../../include/paco_lcs.h"
 #include "ctx.hpp"
@@ -21,7 +22,6 @@
 #include <memory>
 #include <mutex>
 #include <thread>
-#include <unordered_map>
 #include <vector>
 
 namespace paco {
@@ -83,11 +83,26 @@ struct ServeEngine {
     std::mutex mu;
     std::condition_variable cv;
     std::deque<Request *> queue;
-    std::unordered_map<uint64_t, std::unique_ptr<Request>> all;
+    // every live request, indexed by ticket: tickets are handed out in
+    // order, so the table is a deque whose front is ticket `base`; released
+    // entries become null and the front is trimmed
+    std::deque<std::unique_ptr<Request>> table;
+    uint64_t base = 1;
+    Request *find(uint64_t t) {
+        if (t < base || t - base >= table.size()) return nullptr;
+        return table[(size_t)(t - base)].get();
+    }
+    void release(uint64_t t) {
+        table[(size_t)(t - base)].reset();
+        while (!table.empty() && !table.front()) {
+            table.pop_front();
+            ++base;
+        }
+    }
     uint64_t next_ticket = 1;
     size_t budget = 0, in_use = 0;
     bool stop = false;
-    std::thread worker;
+    std::thread workers[kStreams];
     Slot slots[kStreams];
     paco_serve_stats stats{};
     int init_status = PACO_OK;
@@ -120,7 +135,8 @@ int grow_dev(DevBuf &d, size_t need) {
 }
 
 // Launch slot s with the admitted requests in it (engine lock not held).
-int launch_slot(ServeEngine *E, Slot &S) {
+int launch_slot(ServeEngine *E, Slot &S, uint64_t *stage_ns, uint64_t *batch_ns) {
+    const auto t_stage = std::chrono::steady_clock::now();
     const int32_t np = (int32_t)S.reqs.size();
     S.a_off.assign((size_t)np + 1, 0);
     S.b_off.assign((size_t)np + 1, 0);
@@ -172,10 +188,14 @@ int launch_slot(ServeEngine *E, Slot &S) {
     if (na) e = cudaMemcpyAsync(S.a.ptr, S.h_a, na, cudaMemcpyHostToDevice, S.stream);
     if (e == cudaSuccess && nb) e = cudaMemcpyAsync(S.b.ptr, S.h_b, nb, cudaMemcpyHostToDevice, S.stream);
     if (e != cudaSuccess) return PACO_EDEVICE;
+    const auto t_batch = std::chrono::steady_clock::now();
+    *stage_ns = (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(t_batch - t_stage).count();
     int rc = run_batch(E->ctx, S.B, (const uint8_t *)S.a.ptr, S.a_off.data(), (const uint8_t *)S.b.ptr,
                        S.b_off.data(), np, (int32_t *)S.len.ptr, any_want ? (int32_t *)S.rows.ptr : nullptr,
                        S.row_off.data(), any_want ? (int32_t *)S.cols.ptr : nullptr, S.col_off.data(), S.stream,
                        false, 0, E->ctx->opt_alphabet);
+    *batch_ns = (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now() -
+                                                                               t_batch).count();
     if (rc != PACO_OK) return rc;
     e = cudaMemcpyAsync(S.h_len, S.len.ptr, (size_t)np * 4, cudaMemcpyDeviceToHost, S.stream);
     if (e == cudaSuccess && any_want)
@@ -190,7 +210,10 @@ int launch_slot(ServeEngine *E, Slot &S) {
 void complete_slot(ServeEngine *E, Slot &S, int launch_rc) {
     const int dev_err = (launch_rc == PACO_OK && S.h_err) ? *S.h_err : 0;
     if (dev_err != 0) cudaMemsetAsync((int *)S.small.ptr + 1, 0, sizeof(int), S.stream);
-    std::lock_guard<std::mutex> lk(E->mu);
+    // The slot's requests are this worker's until they are marked done, so
+    // their results are filled in and their strings freed without the engine
+    // lock (which the submitters and pollers need).
+    uint64_t cells = 0;
     for (size_t k = 0; k < S.reqs.size(); ++k) {
         Request *r = S.reqs[k];
         r->status = launch_rc != PACO_OK ? launch_rc : dev_err;
@@ -200,84 +223,85 @@ void complete_slot(ServeEngine *E, Slot &S, int launch_rc) {
                 r->row.assign(S.h_rows + S.row_off[k], S.h_rows + S.row_off[k] + r->b.size() + 1);
                 r->col.assign(S.h_cols + S.col_off[k], S.h_cols + S.col_off[k] + r->a.size() + 1);
             }
-            E->stats.cells_done += (uint64_t)r->a.size() * r->b.size();
+            cells += (uint64_t)r->a.size() * r->b.size();
         }
-        r->state = kDone;
-        r->a.clear();
-        r->a.shrink_to_fit();
-        r->b.clear();
-        r->b.shrink_to_fit();
-        E->stats.completed += 1;
+        std::vector<uint8_t>().swap(r->a);
+        std::vector<uint8_t>().swap(r->b);
     }
+    std::lock_guard<std::mutex> lk(E->mu);
+    for (Request *r : S.reqs) r->state = kDone;
+    E->stats.cells_done += cells;
+    E->stats.completed += S.reqs.size();
     E->in_use -= S.bytes;
+    E->stats.inflight_now -= S.reqs.size();
     S.bytes = 0;
     S.reqs.clear();
     S.busy = false;
-    E->stats.inflight_now = 0;
-    for (auto &sl : E->slots) E->stats.inflight_now += sl.reqs.size();
     E->stats.bytes_in_use = E->in_use;
 }
 
-void worker_main(ServeEngine *E) {
+// Admit the queue's front requests into slot S while the budget allows (at
+// most kMaxBatchPairs pairs and about kMaxBatchCells cells); E->mu held.
+void admit(ServeEngine *E, Slot &S) {
+    int64_t cells = 0;
+    while (!E->queue.empty() && (int32_t)S.reqs.size() < kMaxBatchPairs) {
+        Request *r = E->queue.front();
+        const int64_t c = (int64_t)r->a.size() * (int64_t)r->b.size();
+        if (!S.reqs.empty() && cells + c > kMaxBatchCells) break;
+        if (E->in_use + r->bytes > E->budget) break;  // wait for memory to free up
+        E->queue.pop_front();
+        r->state = kRunning;
+        E->in_use += r->bytes;
+        S.bytes += r->bytes;
+        S.reqs.push_back(r);
+        cells += c;
+    }
+    E->stats.queued_now = E->queue.size();
+    E->stats.bytes_in_use = E->in_use;
+}
+
+uint64_t ns_since(std::chrono::steady_clock::time_point t0) {
+    return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now() - t0)
+        .count();
+}
+
+// One worker per stream slot: take the next micro-batch from the queue (FIFO
+// across the workers), prepare and launch it, wait for it, hand its results
+// to the requests.  Host preparation of one slot overlaps the device work of
+// the others.
+void slot_main(ServeEngine *E, int k) {
     cudaSetDevice(E->ctx->device);
+    Slot &S = E->slots[k];
     for (;;) {
-        // completions
-        for (auto &S : E->slots) {
-            if (S.busy && cudaEventQuery(S.done) == cudaSuccess) {
-                const auto t0 = std::chrono::steady_clock::now();
-                complete_slot(E, S, PACO_OK);
-                const uint64_t ns = (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
-                                        std::chrono::steady_clock::now() - t0).count();
-                std::lock_guard<std::mutex> lk(E->mu);
-                E->stats.host_complete_ns += ns;
-            }
-        }
-        // admission: fill one free slot from the queue
-        Slot *free_slot = nullptr;
         {
             std::unique_lock<std::mutex> lk(E->mu);
+            E->cv.wait(lk, [&] {
+                return E->stop || (!E->queue.empty() && E->in_use + E->queue.front()->bytes <= E->budget);
+            });
             if (E->stop) break;
-            for (auto &S : E->slots)
-                if (!S.busy) {
-                    free_slot = &S;
-                    break;
-                }
-            if (free_slot && !E->queue.empty()) {
-                int64_t cells = 0;
-                while (!E->queue.empty() && (int32_t)free_slot->reqs.size() < kMaxBatchPairs) {
-                    Request *r = E->queue.front();
-                    const int64_t c = (int64_t)r->a.size() * (int64_t)r->b.size();
-                    if (!free_slot->reqs.empty() && cells + c > kMaxBatchCells) break;
-                    if (E->in_use + r->bytes > E->budget) break;  // wait for memory to free up
-                    E->queue.pop_front();
-                    r->state = kRunning;
-                    E->in_use += r->bytes;
-                    free_slot->bytes += r->bytes;
-                    free_slot->reqs.push_back(r);
-                    cells += c;
-                }
-                E->stats.queued_now = E->queue.size();
-                E->stats.bytes_in_use = E->in_use;
-            }
-            if (!free_slot || free_slot->reqs.empty()) {
-                bool any_busy = false;
-                for (auto &S : E->slots) any_busy |= S.busy;
-                // nothing to launch: sleep until a submit arrives or a short tick passes
-                E->cv.wait_for(lk, std::chrono::microseconds(any_busy ? 20 : 500));
-                continue;
-            }
-            free_slot->busy = true;
+            admit(E, S);
+            if (S.reqs.empty()) continue;
+            S.busy = true;
             E->stats.batches_launched += 1;
+            E->stats.inflight_now += S.reqs.size();
         }
-        const auto t0 = std::chrono::steady_clock::now();
-        const int rc = launch_slot(E, *free_slot);
-        const uint64_t ns = (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
-                                std::chrono::steady_clock::now() - t0).count();
+        E->cv.notify_one();  // more queued work: the next free worker takes it
+        auto t0 = std::chrono::steady_clock::now();
+        uint64_t stage_ns = 0, batch_ns = 0;
+        const int rc = launch_slot(E, S, &stage_ns, &batch_ns);
+        uint64_t ns = ns_since(t0);
+        if (rc == PACO_OK) cudaEventSynchronize(S.done);
+        t0 = std::chrono::steady_clock::now();
+        complete_slot(E, S, rc);
+        const uint64_t ns2 = ns_since(t0);
         {
             std::lock_guard<std::mutex> lk(E->mu);
             E->stats.host_launch_ns += ns;
+            E->stats.host_complete_ns += ns2;
+            E->stats.host_stage_ns += stage_ns;
+            E->stats.host_batch_ns += batch_ns;
         }
-        if (rc != PACO_OK) complete_slot(E, *free_slot, rc);
+        E->cv.notify_all();  // budget freed: another worker may admit
     }
 }
 
@@ -311,7 +335,7 @@ ServeEngine *serve_get(paco_ctx *ctx, int *rc) {
         S.B = batch_state_new((int *)S.small.ptr, (int *)S.small.ptr + 1);
     }
     ctx->serve = E;
-    E->worker = std::thread(worker_main, E);
+    for (int k = 0; k < kStreams; ++k) E->workers[k] = std::thread(slot_main, E, k);
     *rc = PACO_OK;
     return E;
 }
@@ -324,7 +348,8 @@ void serve_shutdown(paco_ctx *ctx) {
         E->stop = true;
     }
     E->cv.notify_all();
-    if (E->worker.joinable()) E->worker.join();
+    for (auto &t : E->workers)
+        if (t.joinable()) t.join();
     for (auto &S : E->slots) {
         if (S.stream) cudaStreamSynchronize(S.stream);
         batch_state_free(S.B);
@@ -369,7 +394,7 @@ int paco_lcs_submit(paco_ctx *ctx, const uint8_t *a, int64_t n, const uint8_t *b
         r->ticket = E->next_ticket++;
         *ticket = r->ticket;
         E->queue.push_back(r.get());
-        E->all.emplace(r->ticket, std::move(r));
+        E->table.push_back(std::move(r));
         E->stats.submitted += 1;
         E->stats.queued_now = E->queue.size();
     }
@@ -418,7 +443,7 @@ int paco_lcs_submit_many(paco_ctx *ctx, const uint8_t *a_cat, const int64_t *a_o
             r->ticket = E->next_ticket++;
             tickets[taken++] = r->ticket;
             E->queue.push_back(r.get());
-            E->all.emplace(r->ticket, std::move(r));
+            E->table.push_back(std::move(r));
             E->stats.submitted += 1;
         }
         E->stats.queued_now = E->queue.size();
@@ -440,19 +465,18 @@ int paco_lcs_poll_many(paco_ctx *ctx, const uint64_t *tickets, int64_t count, in
     int64_t done = 0;
     std::lock_guard<std::mutex> lk(E->mu);
     for (int64_t k = 0; k < count; ++k) {
-        auto it = E->all.find(tickets[k]);
-        if (it == E->all.end()) {
+        paco::Request *r = E->find(tickets[k]);
+        if (!r) {
             status[k] = PACO_ENOTFOUND;
             continue;
         }
-        paco::Request *r = it->second.get();
         if (r->state != paco::kDone) {
             status[k] = PACO_PENDING;
             continue;
         }
         status[k] = r->status;
         len[k] = r->status == PACO_OK ? r->len : 0;
-        E->all.erase(it);
+        E->release(tickets[k]);
         ++done;
     }
     if (n_done) *n_done = done;
@@ -464,9 +488,8 @@ int paco_lcs_poll(paco_ctx *ctx, uint64_t ticket, int32_t *len, int32_t *row_out
     paco::ServeEngine *E = ctx->serve;
     if (!E) return PACO_ENOTFOUND;
     std::lock_guard<std::mutex> lk(E->mu);
-    auto it = E->all.find(ticket);
-    if (it == E->all.end()) return PACO_ENOTFOUND;
-    paco::Request *r = it->second.get();
+    paco::Request *r = E->find(ticket);
+    if (!r) return PACO_ENOTFOUND;
     if (r->state != paco::kDone) return PACO_PENDING;
     const int st = r->status;
     if (st == PACO_OK) {
@@ -476,7 +499,7 @@ int paco_lcs_poll(paco_ctx *ctx, uint64_t ticket, int32_t *len, int32_t *row_out
             if (col_out) std::memcpy(col_out, r->col.data(), r->col.size() * 4);
         }
     }
-    E->all.erase(it);
+    E->release(ticket);
     return st;
 }
 
