@@ -428,9 +428,11 @@ def paco_lcs_poll(ctx: Context, ticket: int, n: int = 0, m: int = 0, want_bounda
     return int(L.value), row, col
 
 
-def paco_lcs_submit_many(ctx: Context, a_cat, a_off, b_cat, b_off):
+def paco_lcs_submit_many(ctx: Context, a_cat, a_off, b_cat, b_off, partial=False):
     """Submit len(a_off)-1 length-only requests (host arrays) in one call;
-    returns their tickets (uint64 array)."""
+    returns their tickets (uint64 array).  With partial=True a full queue or
+    arena (PACO_EBUSY) is not an error: the tickets of the first requests
+    taken are returned and the caller submits the rest later."""
     import numpy as np
     a_cat = np.ascontiguousarray(a_cat, dtype=np.uint8)
     b_cat = np.ascontiguousarray(b_cat, dtype=np.uint8)
@@ -440,9 +442,11 @@ def paco_lcs_submit_many(ctx: Context, a_cat, a_off, b_cat, b_off):
     t = np.zeros(max(count, 1), dtype=np.uint64)
     taken = ctypes.c_int64(0)
     vp = lambda x: x.ctypes.data_as(ctypes.c_void_p)
-    _check(load().paco_lcs_submit_many(ctx.handle, vp(a_cat), vp(a_off), vp(b_cat), vp(b_off), count, vp(t),
-                                       ctypes.byref(taken)), ctx)
-    return t[:count]
+    rc = load().paco_lcs_submit_many(ctx.handle, vp(a_cat), vp(a_off), vp(b_cat), vp(b_off), count, vp(t),
+                                     ctypes.byref(taken))
+    if not (partial and rc == PACO_EBUSY):
+        _check(rc, ctx)
+    return t[:taken.value]
 
 
 def paco_lcs_poll_many(ctx: Context, tickets):

@@ -1,13 +1,17 @@
 // Serving: continuous batching of LCS requests under a device-memory budget.
 //
-// paco_lcs_submit copies a request into the host queue and returns a ticket.
-// One worker thread per stream slot (kStreams of them) admits queued
-// requests while the budget allows, packs them into a micro-batch and
+// paco_lcs_submit copies a request's strings into pinned host arenas (one
+// for the a strings, one for the b strings, each a FIFO ring) and returns a
+// ticket.  One worker thread per stream slot (kStreams of them) admits queued
+// requests while the device budget allows, packs them into a micro-batch and
 // launches it (the batch engine, one persistent launch) on its slot's
 // stream, so micro-batches overlap on the device and their host preparation
-// runs in parallel; when a micro-batch's completion event fires its results
-// are copied into the requests and their budget is released.  paco_lcs_poll
-// returns PACO_PENDING until then.
+// runs in parallel.  Requests are admitted in submission order, so a
+// micro-batch's strings are one or two contiguous runs of each arena and go
+// to the device in as many copies, straight from where submit put them.
+// When a micro-batch's completion event fires its results are copied into
+// the requests, their budget is released and their arena space reclaimed;
+// paco_lcs_poll returns PACO_PENDING until then.
 #include "../../include/paco_lcs.h"
 #include "ctx.hpp"
 #include "paco_internal.hpp"
@@ -28,19 +32,22 @@ namespace paco {
 
 namespace {
 
-constexpr int kStreams = 4;
+constexpr int kStreams = 8;
 constexpr size_t kMaxQueued = 1u << 20;
 constexpr int32_t kMaxBatchPairs = 8192;
 // Up to ~0.5 ms of device work per micro-batch at the batch kernel's rate:
-// small enough for four to overlap, large enough to amortise each
+// small enough for several to overlap, large enough to amortise each
 // micro-batch's host work (layout, copies, launches).
 constexpr int64_t kMaxBatchCells = 20000000000LL;
+// Pinned arena per string side (a, b).
+constexpr size_t kArenaBytes = (size_t)256 << 20;
 
 enum ReqState { kQueued, kRunning, kDone };
 
 struct Request {
     uint64_t ticket = 0;
-    std::vector<uint8_t> a, b;
+    uint64_t a_pos = 0, b_pos = 0;  // logical arena positions of the strings
+    int64_t n = 0, m = 0;
     bool want = false;
     ReqState state = kQueued;
     int status = PACO_OK;
@@ -59,28 +66,55 @@ size_t request_bytes(int64_t n, int64_t m, bool want) {
     return b;
 }
 
+// A FIFO ring of pinned host memory.  Positions are logical (they only
+// grow); a string never straddles the physical end: when it would, the rest
+// of the lap is skipped.  `tail` is the oldest byte still needed.
+struct Arena {
+    uint8_t *mem = nullptr;
+    size_t cap = 0;
+    uint64_t head = 0;
+    uint64_t tail = 0;
+    // Reserve n contiguous bytes; false when the ring is full.
+    bool reserve(int64_t n, uint64_t *pos) {
+        uint64_t p = head;
+        if ((size_t)(p % cap) + (size_t)n > cap) p += cap - (size_t)(p % cap);  // skip to the next lap
+        if (p + (uint64_t)n - tail > cap) return false;
+        *pos = p;
+        head = p + (uint64_t)n;
+        return true;
+    }
+    uint8_t *at(uint64_t pos) { return mem + (size_t)(pos % cap); }
+};
+
 struct Slot {
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
     BatchState *B = nullptr;
     DevBuf small;             // ticket + error word
     DevBuf a, b, len, rows, cols;
-    // pinned staging
-    uint8_t *h_a = nullptr, *h_b = nullptr;
+    // pinned results
     int32_t *h_len = nullptr, *h_rows = nullptr, *h_cols = nullptr;
     int *h_err = nullptr;
-    size_t cap_a = 0, cap_b = 0, cap_rows = 0, cap_cols = 0, cap_pairs = 0;
+    size_t cap_rows = 0, cap_cols = 0, cap_pairs = 0;
     std::vector<Request *> reqs;
     std::vector<int64_t> a_off, b_off, row_off, col_off;
     bool busy = false;
     size_t bytes = 0;
+    uint64_t seq = 0;  // admission number of the micro-batch (arena reclaim order)
+};
+
+// Arena space of one admitted micro-batch, reclaimed in admission order.
+struct Held {
+    uint64_t seq, a_end, b_end;
+    bool done;
 };
 
 }  // namespace
 
 struct ServeEngine {
     paco_ctx *ctx = nullptr;
-    std::mutex mu;
+    std::mutex mu;       // queue, request table, budget, stats, arena tails, reclaim list
+    std::mutex sub_mu;   // submitters: arena reservation and copy, in ticket order
     std::condition_variable cv;
     std::deque<Request *> queue;
     // every live request, indexed by ticket: tickets are handed out in
@@ -100,6 +134,9 @@ struct ServeEngine {
         }
     }
     uint64_t next_ticket = 1;
+    Arena arena_a, arena_b;   // heads move under sub_mu and mu, tails under mu
+    std::deque<Held> held;
+    uint64_t next_seq = 0;
     size_t budget = 0, in_use = 0;
     bool stop = false;
     std::thread workers[kStreams];
@@ -123,15 +160,41 @@ int grow_pinned(void **p, size_t *cap, size_t need) {
     return PACO_OK;
 }
 
-int grow_dev(DevBuf &d, size_t need) {
+// Stream-ordered growth of a slot's device buffer (no device-wide sync).
+int grow_dev(DevBuf &d, size_t need, cudaStream_t st) {
     if (d.bytes >= need) return PACO_OK;
-    if (d.ptr) cudaFree(d.ptr);
+    if (d.ptr) cudaFreeAsync(d.ptr, st);
     d.ptr = nullptr;
     d.bytes = 0;
     size_t want = need < 4096 ? 4096 : need * 2;
-    if (cudaMalloc(&d.ptr, want) != cudaSuccess) return PACO_ENOMEM;
+    if (cudaMallocAsync(&d.ptr, want, st) != cudaSuccess) return PACO_ENOMEM;
     d.bytes = want;
     return PACO_OK;
+}
+
+// One side's strings of a micro-batch to the device: the runs of requests
+// whose strings follow each other in the arena, one copy per run.
+cudaError_t copy_side(Arena &ar, const std::vector<Request *> &reqs, bool side_a, uint8_t *dst, cudaStream_t st) {
+    size_t k = 0, out = 0;
+    while (k < reqs.size()) {
+        const uint64_t start = side_a ? reqs[k]->a_pos : reqs[k]->b_pos;
+        uint64_t end = start;
+        size_t j = k;
+        while (j < reqs.size()) {
+            const uint64_t p = side_a ? reqs[j]->a_pos : reqs[j]->b_pos;
+            const int64_t len = side_a ? reqs[j]->n : reqs[j]->m;
+            if (p != end) break;
+            end = p + (uint64_t)len;
+            ++j;
+        }
+        if (end > start) {
+            cudaError_t e = cudaMemcpyAsync(dst + out, ar.at(start), (size_t)(end - start), cudaMemcpyHostToDevice, st);
+            if (e != cudaSuccess) return e;
+            out += (size_t)(end - start);
+        }
+        k = j;
+    }
+    return cudaSuccess;
 }
 
 // Launch slot s with the admitted requests in it (engine lock not held).
@@ -146,23 +209,16 @@ int launch_slot(ServeEngine *E, Slot &S, uint64_t *stage_ns, uint64_t *batch_ns)
     int64_t rows_tot = 0, cols_tot = 0;
     for (int32_t k = 0; k < np; ++k) {
         Request *r = S.reqs[(size_t)k];
-        S.a_off[(size_t)k + 1] = S.a_off[(size_t)k] + (int64_t)r->a.size();
-        S.b_off[(size_t)k + 1] = S.b_off[(size_t)k] + (int64_t)r->b.size();
+        S.a_off[(size_t)k + 1] = S.a_off[(size_t)k] + r->n;
+        S.b_off[(size_t)k + 1] = S.b_off[(size_t)k] + r->m;
         S.row_off[(size_t)k] = rows_tot;
         S.col_off[(size_t)k] = cols_tot;
-        rows_tot += (int64_t)r->b.size() + 1;
-        cols_tot += (int64_t)r->a.size() + 1;
+        rows_tot += r->m + 1;
+        cols_tot += r->n + 1;
         any_want |= r->want;
     }
     const size_t na = (size_t)S.a_off[(size_t)np], nb = (size_t)S.b_off[(size_t)np];
-    size_t cap;
-    cap = S.cap_a;
-    if (grow_pinned((void **)&S.h_a, &cap, na + 16) != PACO_OK) return PACO_ENOMEM;
-    S.cap_a = cap;
-    cap = S.cap_b;
-    if (grow_pinned((void **)&S.h_b, &cap, nb + 16) != PACO_OK) return PACO_ENOMEM;
-    S.cap_b = cap;
-    cap = S.cap_pairs;
+    size_t cap = S.cap_pairs;
     if (grow_pinned((void **)&S.h_len, &cap, (size_t)np * 4 + 16) != PACO_OK) return PACO_ENOMEM;
     S.cap_pairs = cap;
     if (any_want) {
@@ -173,20 +229,14 @@ int launch_slot(ServeEngine *E, Slot &S, uint64_t *stage_ns, uint64_t *batch_ns)
         if (grow_pinned((void **)&S.h_cols, &cap, (size_t)cols_tot * 4 + 16) != PACO_OK) return PACO_ENOMEM;
         S.cap_cols = cap;
     }
-    for (int32_t k = 0; k < np; ++k) {
-        Request *r = S.reqs[(size_t)k];
-        if (!r->a.empty()) std::memcpy(S.h_a + S.a_off[(size_t)k], r->a.data(), r->a.size());
-        if (!r->b.empty()) std::memcpy(S.h_b + S.b_off[(size_t)k], r->b.data(), r->b.size());
-    }
-    if (grow_dev(S.a, na + 16) != PACO_OK || grow_dev(S.b, nb + 16) != PACO_OK ||
-        grow_dev(S.len, (size_t)np * 4 + 16) != PACO_OK)
+    if (grow_dev(S.a, na + 16, S.stream) != PACO_OK || grow_dev(S.b, nb + 16, S.stream) != PACO_OK ||
+        grow_dev(S.len, (size_t)np * 4 + 16, S.stream) != PACO_OK)
         return PACO_ENOMEM;
-    if (any_want && (grow_dev(S.rows, (size_t)rows_tot * 4 + 16) != PACO_OK ||
-                     grow_dev(S.cols, (size_t)cols_tot * 4 + 16) != PACO_OK))
+    if (any_want && (grow_dev(S.rows, (size_t)rows_tot * 4 + 16, S.stream) != PACO_OK ||
+                     grow_dev(S.cols, (size_t)cols_tot * 4 + 16, S.stream) != PACO_OK))
         return PACO_ENOMEM;
-    cudaError_t e = cudaSuccess;
-    if (na) e = cudaMemcpyAsync(S.a.ptr, S.h_a, na, cudaMemcpyHostToDevice, S.stream);
-    if (e == cudaSuccess && nb) e = cudaMemcpyAsync(S.b.ptr, S.h_b, nb, cudaMemcpyHostToDevice, S.stream);
+    cudaError_t e = copy_side(E->arena_a, S.reqs, true, (uint8_t *)S.a.ptr, S.stream);
+    if (e == cudaSuccess) e = copy_side(E->arena_b, S.reqs, false, (uint8_t *)S.b.ptr, S.stream);
     if (e != cudaSuccess) return PACO_EDEVICE;
     const auto t_batch = std::chrono::steady_clock::now();
     *stage_ns = (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(t_batch - t_stage).count();
@@ -211,8 +261,8 @@ void complete_slot(ServeEngine *E, Slot &S, int launch_rc) {
     const int dev_err = (launch_rc == PACO_OK && S.h_err) ? *S.h_err : 0;
     if (dev_err != 0) cudaMemsetAsync((int *)S.small.ptr + 1, 0, sizeof(int), S.stream);
     // The slot's requests are this worker's until they are marked done, so
-    // their results are filled in and their strings freed without the engine
-    // lock (which the submitters and pollers need).
+    // their results are filled in without the engine lock (which the
+    // submitters and pollers need).
     uint64_t cells = 0;
     for (size_t k = 0; k < S.reqs.size(); ++k) {
         Request *r = S.reqs[k];
@@ -220,13 +270,11 @@ void complete_slot(ServeEngine *E, Slot &S, int launch_rc) {
         if (r->status == PACO_OK) {
             r->len = S.h_len[k];
             if (r->want) {
-                r->row.assign(S.h_rows + S.row_off[k], S.h_rows + S.row_off[k] + r->b.size() + 1);
-                r->col.assign(S.h_cols + S.col_off[k], S.h_cols + S.col_off[k] + r->a.size() + 1);
+                r->row.assign(S.h_rows + S.row_off[k], S.h_rows + S.row_off[k] + r->m + 1);
+                r->col.assign(S.h_cols + S.col_off[k], S.h_cols + S.col_off[k] + r->n + 1);
             }
-            cells += (uint64_t)r->a.size() * r->b.size();
+            cells += (uint64_t)r->n * (uint64_t)r->m;
         }
-        std::vector<uint8_t>().swap(r->a);
-        std::vector<uint8_t>().swap(r->b);
     }
     std::lock_guard<std::mutex> lk(E->mu);
     for (Request *r : S.reqs) r->state = kDone;
@@ -234,6 +282,14 @@ void complete_slot(ServeEngine *E, Slot &S, int launch_rc) {
     E->stats.completed += S.reqs.size();
     E->in_use -= S.bytes;
     E->stats.inflight_now -= S.reqs.size();
+    // reclaim the arena space of the micro-batches completed so far, oldest first
+    for (Held &h : E->held)
+        if (h.seq == S.seq) h.done = true;
+    while (!E->held.empty() && E->held.front().done) {
+        E->arena_a.tail = E->held.front().a_end;
+        E->arena_b.tail = E->held.front().b_end;
+        E->held.pop_front();
+    }
     S.bytes = 0;
     S.reqs.clear();
     S.busy = false;
@@ -244,9 +300,10 @@ void complete_slot(ServeEngine *E, Slot &S, int launch_rc) {
 // most kMaxBatchPairs pairs and about kMaxBatchCells cells); E->mu held.
 void admit(ServeEngine *E, Slot &S) {
     int64_t cells = 0;
+    uint64_t a_end = 0, b_end = 0;
     while (!E->queue.empty() && (int32_t)S.reqs.size() < kMaxBatchPairs) {
         Request *r = E->queue.front();
-        const int64_t c = (int64_t)r->a.size() * (int64_t)r->b.size();
+        const int64_t c = r->n * r->m;
         if (!S.reqs.empty() && cells + c > kMaxBatchCells) break;
         if (E->in_use + r->bytes > E->budget) break;  // wait for memory to free up
         E->queue.pop_front();
@@ -255,6 +312,12 @@ void admit(ServeEngine *E, Slot &S) {
         S.bytes += r->bytes;
         S.reqs.push_back(r);
         cells += c;
+        a_end = r->a_pos + (uint64_t)r->n;
+        b_end = r->b_pos + (uint64_t)r->m;
+    }
+    if (!S.reqs.empty()) {
+        S.seq = E->next_seq++;
+        E->held.push_back(Held{S.seq, a_end, b_end, false});
     }
     E->stats.queued_now = E->queue.size();
     E->stats.bytes_in_use = E->in_use;
@@ -305,6 +368,41 @@ void slot_main(ServeEngine *E, int k) {
     }
 }
 
+// Copy a request's strings into the arenas and queue it (the caller holds
+// sub_mu, so heads move in ticket order; the tails are read under mu).
+// PACO_EBUSY when an arena, the queue or the budget cannot take it.
+int enqueue(ServeEngine *E, const uint8_t *a, int64_t n, const uint8_t *b, int64_t m, bool want, uint64_t *ticket) {
+    const size_t bytes = request_bytes(n, m, want);
+    if (bytes > E->budget || (size_t)n > E->arena_a.cap || (size_t)m > E->arena_b.cap) return PACO_EBUSY;
+    Arena ta, tb;
+    {
+        std::lock_guard<std::mutex> lk(E->mu);
+        if (E->queue.size() >= kMaxQueued) return PACO_EBUSY;
+        ta = E->arena_a;
+        tb = E->arena_b;
+    }
+    auto r = std::make_unique<Request>();
+    if (!ta.reserve(n, &r->a_pos) || !tb.reserve(m, &r->b_pos)) return PACO_EBUSY;
+    // the reserved bytes lie past every admitted request's, so no reader
+    // touches them until this request is queued
+    if (n) std::memcpy(ta.at(r->a_pos), a, (size_t)n);
+    if (m) std::memcpy(tb.at(r->b_pos), b, (size_t)m);
+    r->n = n;
+    r->m = m;
+    r->want = want;
+    r->bytes = bytes;
+    std::lock_guard<std::mutex> lk(E->mu);
+    E->arena_a.head = ta.head;
+    E->arena_b.head = tb.head;
+    r->ticket = E->next_ticket++;
+    *ticket = r->ticket;
+    E->queue.push_back(r.get());
+    E->table.push_back(std::move(r));
+    E->stats.submitted += 1;
+    E->stats.queued_now = E->queue.size();
+    return PACO_OK;
+}
+
 }  // namespace
 
 ServeEngine *serve_get(paco_ctx *ctx, int *rc) {
@@ -320,6 +418,14 @@ ServeEngine *serve_get(paco_ctx *ctx, int *rc) {
     E->ctx = ctx;
     E->budget = ctx->budget;
     E->stats.bytes_budget = ctx->budget;
+    ctx->serve = E;
+    if (cudaMallocHost((void **)&E->arena_a.mem, kArenaBytes) != cudaSuccess ||
+        cudaMallocHost((void **)&E->arena_b.mem, kArenaBytes) != cudaSuccess) {
+        *rc = PACO_ENOMEM;
+        E->init_status = PACO_ENOMEM;
+        return E;
+    }
+    E->arena_a.cap = E->arena_b.cap = kArenaBytes;
     for (auto &S : E->slots) {
         if (cudaStreamCreateWithFlags(&S.stream, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&S.done, cudaEventDisableTiming) != cudaSuccess ||
@@ -327,14 +433,19 @@ ServeEngine *serve_get(paco_ctx *ctx, int *rc) {
             cudaMallocHost((void **)&S.h_err, 64) != cudaSuccess) {
             *rc = PACO_EDEVICE;
             E->init_status = PACO_EDEVICE;
-            ctx->serve = E;
             return E;
         }
         S.small.bytes = 256;
         *S.h_err = 0;
+        // the lengths of a full micro-batch, pinned up front (growing pinned
+        // memory later would stall the worker for milliseconds)
+        if (grow_pinned((void **)&S.h_len, &S.cap_pairs, (size_t)kMaxBatchPairs * 4 + 16) != PACO_OK) {
+            *rc = PACO_ENOMEM;
+            E->init_status = PACO_ENOMEM;
+            return E;
+        }
         S.B = batch_state_new((int *)S.small.ptr, (int *)S.small.ptr + 1);
     }
-    ctx->serve = E;
     for (int k = 0; k < kStreams; ++k) E->workers[k] = std::thread(slot_main, E, k);
     *rc = PACO_OK;
     return E;
@@ -355,12 +466,13 @@ void serve_shutdown(paco_ctx *ctx) {
         batch_state_free(S.B);
         for (DevBuf *d : {&S.small, &S.a, &S.b, &S.len, &S.rows, &S.cols})
             if (d->ptr) cudaFree(d->ptr);
-        for (void *h : {(void *)S.h_a, (void *)S.h_b, (void *)S.h_len, (void *)S.h_rows, (void *)S.h_cols,
-                        (void *)S.h_err})
+        for (void *h : {(void *)S.h_len, (void *)S.h_rows, (void *)S.h_cols, (void *)S.h_err})
             if (h) cudaFreeHost(h);
         if (S.done) cudaEventDestroy(S.done);
         if (S.stream) cudaStreamDestroy(S.stream);
     }
+    if (E->arena_a.mem) cudaFreeHost(E->arena_a.mem);
+    if (E->arena_b.mem) cudaFreeHost(E->arena_b.mem);
     delete E;
     ctx->serve = nullptr;
 }
@@ -381,25 +493,12 @@ int paco_lcs_submit(paco_ctx *ctx, const uint8_t *a, int64_t n, const uint8_t *b
         E = paco::serve_get(ctx, &rc);
     }
     if (!E || rc != PACO_OK) return rc;
-    const size_t bytes = paco::request_bytes(n, m, want_boundaries != 0);
-    if (bytes > E->budget) return PACO_EBUSY;
-    auto r = std::make_unique<paco::Request>();
-    r->a.assign(a, a + n);
-    r->b.assign(b, b + m);
-    r->want = want_boundaries != 0;
-    r->bytes = bytes;
     {
-        std::lock_guard<std::mutex> lk(E->mu);
-        if (E->queue.size() >= paco::kMaxQueued) return PACO_EBUSY;
-        r->ticket = E->next_ticket++;
-        *ticket = r->ticket;
-        E->queue.push_back(r.get());
-        E->table.push_back(std::move(r));
-        E->stats.submitted += 1;
-        E->stats.queued_now = E->queue.size();
+        std::lock_guard<std::mutex> lk(E->sub_mu);
+        rc = paco::enqueue(E, a, n, b, m, want_boundaries != 0, ticket);
     }
-    E->cv.notify_one();
-    return PACO_OK;
+    if (rc == PACO_OK) E->cv.notify_one();
+    return rc;
 }
 
 int paco_lcs_submit_many(paco_ctx *ctx, const uint8_t *a_cat, const int64_t *a_off, const uint8_t *b_cat,
@@ -419,34 +518,16 @@ int paco_lcs_submit_many(paco_ctx *ctx, const uint8_t *a_cat, const int64_t *a_o
         E = paco::serve_get(ctx, &rc);
     }
     if (!E || rc != PACO_OK) return rc;
-    // copy the strings outside the engine lock
-    std::vector<std::unique_ptr<paco::Request>> rs;
-    rs.reserve((size_t)count);
-    for (int64_t k = 0; k < count; ++k) {
-        const int64_t n = a_off[k + 1] - a_off[k], m = b_off[k + 1] - b_off[k];
-        auto r = std::make_unique<paco::Request>();
-        r->a.assign(a_cat + a_off[k], a_cat + a_off[k] + n);
-        r->b.assign(b_cat + b_off[k], b_cat + b_off[k] + m);
-        r->want = false;
-        r->bytes = paco::request_bytes(n, m, false);
-        rs.push_back(std::move(r));
-    }
     int64_t taken = 0;
-    rc = PACO_OK;
     {
-        std::lock_guard<std::mutex> lk(E->mu);
-        for (auto &r : rs) {
-            if (r->bytes > E->budget || E->queue.size() >= paco::kMaxQueued) {
-                rc = PACO_EBUSY;
-                break;
-            }
-            r->ticket = E->next_ticket++;
-            tickets[taken++] = r->ticket;
-            E->queue.push_back(r.get());
-            E->table.push_back(std::move(r));
-            E->stats.submitted += 1;
+        std::lock_guard<std::mutex> lk(E->sub_mu);
+        for (int64_t k = 0; k < count; ++k) {
+            const int64_t n = a_off[k + 1] - a_off[k], m = b_off[k + 1] - b_off[k];
+            rc = paco::enqueue(E, a_cat + a_off[k], n, b_cat + b_off[k], m, false, &tickets[k]);
+            if (rc != PACO_OK) break;
+            ++taken;
+            if ((taken & 63) == 0) E->cv.notify_one();  // let a worker start on a long submission
         }
-        E->stats.queued_now = E->queue.size();
     }
     if (n_submitted) *n_submitted = taken;
     if (taken) E->cv.notify_one();

@@ -268,3 +268,43 @@ def test_serve_budget_and_tickets():
         assert e.value.status == P.PACO_ENOTFOUND
     finally:
         c.close()
+
+
+def test_serve_arena_laps_and_full_arena(ctx):
+    """Serving copies request strings into pinned FIFO arenas of 256 MiB per
+    side: 150 requests with 4 MiB a-strings (600 MiB in all) lap the a-arena
+    twice, a full arena answers PACO_EBUSY (the partial submit stops there),
+    and space comes back as micro-batches complete.  b is one symbol, so
+    L = 1 exactly when a holds it."""
+    k_total = 150
+    n = 4 << 20
+    pending, got, k = {}, {}, 0
+    t0 = time.time()
+    while len(got) < k_total:
+        assert time.time() - t0 < 300
+        if k < k_total:
+            syms = [np.uint8(3 if (j * 7) % 5 else 9) for j in range(k, min(k_total, k + 8))]
+            a_list = [np.full(n, j % 3, np.uint8) for j in range(k, k + len(syms))]
+            for a, j in zip(a_list, range(k, k + len(syms))):
+                a[(j * 977) % n] = 9 if j % 4 == 0 else 1  # a holds 9 only when j % 4 == 0
+            a_cat = np.concatenate(a_list)
+            a_off = np.arange(len(syms) + 1, dtype=np.int64) * n
+            b_cat = np.array(syms, np.uint8)
+            b_off = np.arange(len(syms) + 1, dtype=np.int64)
+            t = P.paco_lcs_submit_many(ctx, a_cat, a_off, b_cat, b_off, partial=True)
+            for i, ticket in enumerate(t):
+                pending[int(ticket)] = k + i
+            k += len(t)
+        if pending:
+            tick = np.array(list(pending), np.uint64)
+            st, ln = P.paco_lcs_poll_many(ctx, tick)
+            for ticket, s_, l_ in zip(tick, st, ln):
+                if s_ != P.PACO_PENDING:
+                    assert s_ == P.PACO_OK
+                    got[pending.pop(int(ticket))] = int(l_)
+        time.sleep(0.001)
+    # a holds the symbols j % 3 and one 9 (j % 4 == 0) or one 1; b is 3 (never
+    # in a) unless j % 5 == 0, when it is 9
+    for j in range(k_total):
+        want = 1 if (j % 5 == 0 and j % 4 == 0) else 0
+        assert got[j] == want, (j, got[j])
