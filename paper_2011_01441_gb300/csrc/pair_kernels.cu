@@ -287,6 +287,12 @@ __global__ void __launch_bounds__(256, 1) k_pair_bp(const PairArgs P) {
                 int minc = cons[0];
                 for (int v = 1; v < W; ++v) minc = min(minc, cons[v]);
                 const int lim_c = min(nvwords, minc - 1 - kLagW + R);
+                // the strip above's next words: loaded first, so their latency
+                // overlaps the column work below
+                const int lim_s = min(nwords, cons[0] + kSrcSlots - 1);
+                const int qp = qs + lane;
+                uint64_t vp = 0;
+                if (s > 0 && qp < lim_s) vp = ld_relaxed_u64(src_row + qp);
                 if (qc < lim_c) {
                     const int qe = min(lim_c, qc + 8);
                     uint32_t o[8];
@@ -308,16 +314,11 @@ __global__ void __launch_bounds__(256, 1) k_pair_bp(const PairArgs P) {
                     qc = qe;
                     progress = true;
                 }
-                const int lim_s = min(nwords, cons[0] + kSrcSlots - 1);
                 if (qs < lim_s) {
                     if (s > 0) {  // the strip above's output words, as they are published
-                        const int q = qs + lane;
-                        uint64_t v = 0;
-                        bool rd = false;
-                        if (q < lim_s) {
-                            v = ld_relaxed_u64(src_row + q);
-                            rd = (uint32_t)(v >> 32) == want;
-                        }
+                        const int q = qp;
+                        const uint64_t v = vp;
+                        const bool rd = q < lim_s && (uint32_t)(v >> 32) == want;
                         const uint32_t bal = __ballot_sync(kFull, rd);
                         const int n = (bal == kFull) ? 32 : (__ffs(~bal) - 1);
                         if (lane < n) srcq[q & (kSrcSlots - 1)] = ((uint64_t)(uint32_t)(q + 1) << 32) | (uint32_t)v;
@@ -392,7 +393,9 @@ __global__ void __launch_bounds__(256, 1) k_pair_bp(const PairArgs P) {
                             break;
                         }
                     }
-                    if (idle > 4) __nanosleep(idle > 64 ? 256 : 32);
+                    // short naps while the strip above is publishing (its next
+                    // word is on the critical path), longer ones otherwise
+                    if (idle > 4) __nanosleep(idle > 64 && !(s > 0 && qs < nwords && qs > 0) ? 256 : 32);
                 }
             }
             if (ok && last_strip && lane == 0 && P.len) P.len[0] = run;
