@@ -29,6 +29,11 @@ namespace {
 
 using namespace dev;
 
+static __device__ __forceinline__ void st_u32_if(bool p, uint32_t *ptr, uint32_t v) {
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %0, 0;\n\t@q st.global.u32 [%1], %2;\n\t}"
+                 ::"r"((uint32_t)p), "l"(ptr), "r"(v));
+}
+
 enum : uint32_t {
     kTransposed = 1u,
     kInGlobal = 2u,   // top carries from tagged words of an earlier job
@@ -144,8 +149,6 @@ static __device__ __noinline__ void wait_done(const uint32_t *flag, uint32_t wan
     }
 }
 
-constexpr int kBatchSrcRing = 8;
-constexpr int kBatchSrcAhead = 4;
 // Column offsets reach the warp through a shared ring of 32-column words,
 // copied kColAhead words ahead (lane 31 trails lane 0 by at most 31*8/32 + 1
 // = 9 words); two mirror slots after the ring repeat slots 0 and 1, so a
@@ -159,7 +162,7 @@ constexpr int kColAhead = 8;
 template <int C, bool TILES>
 static __device__ __forceinline__ void batch_job(const BatchArgs &P, const SegJob &J, const int lane, uint32_t *pm,
                                                  const uint32_t pm_lane, uint32_t *cols_ptr, const uint32_t col_ring,
-                                                 const uint32_t src_ring, const uint32_t epoch) {
+                                                 const uint32_t epoch) {
     constexpr int K = 32 / C;
     {
         const bool tr = (J.flags & kTransposed) != 0;
@@ -199,29 +202,20 @@ static __device__ __forceinline__ void batch_job(const BatchArgs &P, const SegJo
                 0x80000000u;
         __syncwarp();
 
-        const int64_t nwords = (S + 31) >> 5;
-        const int64_t npairs = (nwords + 1) >> 1;
-        const int last = (J.nrows - 1) / kLaneRows;      // last real lane: the pipeline's end
+        // the job's scalars, broadcast from lane 0 so the compiler sees them
+        // as warp-uniform (uniform branches, no reconvergence barriers)
+        const int nwords = __shfl_sync(kFull, (int)((S + 31) >> 5), 0);
+        const int last = __shfl_sync(kFull, (J.nrows - 1) / kLaneRows, 0);  // last real lane: the pipeline's end
         const int flush_i = (last + K - 1) % K;         // step at which it completes a word
         // words lane 0 runs over: the real ones, then zero-row words until the
         // last lane has finished the last real word
-        const int64_t nouter = (nwords * K + last + K - 1) / K;
-        const bool in_global = (J.flags & kInGlobal) != 0;
-        const bool out_global = (J.flags & kOutGlobal) != 0;
+        const int nouter = (nwords * K + last + K - 1) / K;
+        const bool in_global = __shfl_sync(kFull, (J.flags & kInGlobal) != 0 ? 1 : 0, 0) != 0;
+        const bool out_global = __shfl_sync(kFull, (J.flags & kOutGlobal) != 0 ? 1 : 0, 0) != 0;
         const uint64_t *src_row = P.hbuf + J.hin;
         uint64_t *dst_row = P.hbuf + J.hout;
         uint32_t *bout = P.bbits + (J.bword >= 0 ? J.bword : 0);
         const bool keep_bits = !out_global && J.bword >= 0;
-        auto issue_pair = [&](int64_t pr) {
-            if (pr < npairs) {
-                const uint32_t dst = src_ring + (uint32_t)((pr % kBatchSrcRing) * 16);
-                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src_row + 2 * pr)
-                             : "memory");
-            }
-            asm volatile("cp.async.commit_group;" ::: "memory");
-        };
-        if (in_global && lane == 0)
-            for (int d = 0; d < kBatchSrcAhead; ++d) issue_pair(d);
 
         uint32_t cw = 0;      // this lane's carry-outs, newest in bit 0 (never reset)
         uint32_t sr = 0;      // carry-ins, next one in bit 31
@@ -230,13 +224,13 @@ static __device__ __forceinline__ void batch_job(const BatchArgs &P, const SegJo
         // lanes 0..7 copy one 32-column word (16 bytes each); lanes 8..15 the
         // mirror copy when the word lands in slot 0 or 1.  Columns at or past
         // S are zero-filled: offset 0 is the all-zero match row.
-        auto issue_cols = [&](int64_t wd) {
-            const int slot = (int)(wd % kColRing);
+        auto issue_cols = [&](int wd) {
+            const int slot = wd & (kColRing - 1);
             const int part = lane & 7;
             if (lane < 8 || (lane < 16 && slot < 2)) {
-                const int64_t col = wd * 32 + part * 4;
-                const int64_t rem = S - col;
-                const int bytes = rem >= 4 ? 16 : (rem > 0 ? (int)rem * 4 : 0);
+                const int col = wd * 32 + part * 4;
+                const int rem = (int)S - col;
+                const int bytes = rem >= 4 ? 16 : (rem > 0 ? rem * 4 : 0);
                 const uint32_t *src = boff + (bytes > 0 ? col : 0);
                 const int dslot = lane < 8 ? slot : kColRing + slot;
                 const uint32_t dst = col_ring + (uint32_t)((dslot * 32 + part * 4) * 4);
@@ -272,56 +266,80 @@ static __device__ __forceinline__ void batch_job(const BatchArgs &P, const SegJo
             __syncwarp();
         }
         for (int d = 0; d < kColAhead; ++d) issue_cols(d);
-        for (int64_t u = 0; u < nouter; ++u) {
+        // Lane 0's input carry words (segments below another segment of the
+        // pair): loaded from global memory two words ahead into registers;
+        // a stale tag sends the warp to the slow path outside the word loop.
+        uint64_t in0 = 0, in1 = 0;
+        if (in_global) {
+            in0 = ld_relaxed_u64(src_row + 0);
+            if (nwords > 1) in1 = ld_relaxed_u64(src_row + 1);
+        }
+        // the first word's match words and the offsets one step after them
+        uint32_t Mcur[C], onext[C];
+        {
+            const int c0 = -C * lane;
+            const uint32_t cb0 = col_ring + (uint32_t)(((c0 >> 5) & (kColRing - 1)) * 128) + (uint32_t)((c0 & 31) * 4);
             asm volatile("cp.async.wait_group %0;" ::"n"(kColAhead - 1) : "memory");
             __syncwarp();
-            issue_cols(u + kColAhead);
-            uint32_t srcw = 0;
-            bool lok = true;
-            if (lane == 0 && in_global && u < nwords) {
-                if ((u & 1) == 0) {
-                    asm volatile("cp.async.wait_group %0;" ::"n"(kBatchSrcAhead - 1) : "memory");
-                    issue_pair((u >> 1) + kBatchSrcAhead);
-                }
-                const uint32_t slot = src_ring + (uint32_t)((((u >> 1) % kBatchSrcRing) * 16) + (u & 1) * 8);
-                uint64_t v;
-                asm volatile("ld.shared.u64 %0, [%1];" : "=l"(v) : "r"(slot) : "memory");
-                if ((uint32_t)(v >> 32) != epoch) v = poll_global_lane(src_row + u, epoch, P.err, P.wait_limit_ns, lok);
-                srcw = (uint32_t)v;
-            }
-            if (in_global && !__all_sync(kFull, lok)) {
-                ok = false;
-                break;
-            }
-            if (lane == 0) sr = srcw;
-            const int64_t ubase = u * K;
-            // this lane's column of step 0 (lane k trails lane 0 by k chunks) in the ring
-            const int64_t c0 = u * 32 - (int64_t)C * lane;
-            const uint32_t cbase = col_ring + (uint32_t)(((c0 >> 5) & (kColRing - 1)) * 128) + (uint32_t)((c0 & 31) * 4);
-            // one loop for fill, steady state and drain: columns outside [0, S)
-            // read the zero row, so an idle lane keeps its state and passes
-            // zero carries
-            uint32_t ocur[C], onext[C];
-            offs_at(cbase, ocur);
+            uint32_t o0[C];
+            offs_at(cb0, o0);
 #pragma unroll
-            for (int i = 0; i < K; ++i) {
-                if (i + 1 < K) offs_at(cbase + (uint32_t)((i + 1) * C * 4), onext);
-                const uint32_t up = __shfl_up_sync(kFull, cw, 1);
-                if (lane != 0) sr = up << (32 - C);
+            for (int jj = 0; jj < C; ++jj) Mcur[jj] = lds_u32(pm_lane + o0[jj]);
+            offs_at(cb0 + (uint32_t)(C * 4), onext);
+        }
+        int u = 0;
+        for (;;) {
+            for (; u < nouter; ++u) {
+                // lane 0's input carry word u, checked by a vote (uniform exit)
+                if (in_global && u < nwords &&
+                    !__all_sync(kFull, lane != 0 || (uint32_t)(in0 >> 32) == epoch))
+                    break;
+                // words up to u + 1 copied (the last steps read into the next word)
+                asm volatile("cp.async.wait_group %0;" ::"n"(kColAhead - 2) : "memory");
+                __syncwarp();
+                issue_cols(u + kColAhead);
+                const uint32_t srcw = (in_global && u < nwords) ? (uint32_t)in0 : 0u;
+                in0 = in1;
+                if (in_global && u + 2 < nwords) in1 = ld_relaxed_u64(src_row + u + 2);
+                if (lane == 0) sr = srcw;
+                const int ubase = u * K;
+                // this lane's column of step 0 (lane k trails lane 0 by k chunks) in the ring
+                const int c0 = u * 32 - C * lane;
+                const uint32_t cbase = col_ring + (uint32_t)(((c0 >> 5) & (kColRing - 1)) * 128) + (uint32_t)((c0 & 31) * 4);
+                // one loop for fill, steady state and drain: columns outside [0, S)
+                // read the zero row, so an idle lane keeps its state and passes
+                // zero carries.  Offsets two steps ahead, match words one.
 #pragma unroll
-                for (int jj = 0; jj < C; ++jj) column31v(V, sr, cw, lds_u32(pm_lane + ocur[jj]));
+                for (int i = 0; i < K; ++i) {
+                    uint32_t onext2[C], Mnext[C];
+                    offs_at(cbase + (uint32_t)((i + 2) * C * 4), onext2);
 #pragma unroll
-                for (int jj = 0; jj < C; ++jj) ocur[jj] = onext[jj];
-                if (i == flush_i) {  // the last lane completes word wq
-                    const int64_t wq = ((ubase + i - last) * C) >> 5;
-                    const bool fl = lane == last && wq >= 0 && wq < nwords;
-                    if (out_global) {
-                        st_relaxed_u64_if(fl, dst_row + (fl ? wq : 0), ((uint64_t)epoch << 32) | cw);
-                    } else if (fl) {
-                        total += __popc(cw);
-                        if (keep_bits) bout[wq] = cw;
+                    for (int jj = 0; jj < C; ++jj) Mnext[jj] = lds_u32(pm_lane + onext[jj]);
+                    const uint32_t up = __shfl_up_sync(kFull, cw, 1);
+                    if (lane != 0) sr = up << (32 - C);
+#pragma unroll
+                    for (int jj = 0; jj < C; ++jj) column31v(V, sr, cw, Mcur[jj]);
+#pragma unroll
+                    for (int jj = 0; jj < C; ++jj) {
+                        Mcur[jj] = Mnext[jj];
+                        onext[jj] = onext2[jj];
+                    }
+                    if (i == flush_i) {  // the last lane completes word wq (predicated stores)
+                        const int wq = ((ubase + i - last) * C) >> 5;
+                        const bool fl = lane == last && wq >= 0 && wq < nwords;
+                        st_relaxed_u64_if(fl && out_global, dst_row + (fl ? wq : 0), ((uint64_t)epoch << 32) | cw);
+                        total += (fl && !out_global) ? (uint32_t)__popc(cw) : 0u;
+                        st_u32_if(fl && keep_bits, bout + (fl ? wq : 0), cw);
                     }
                 }
+            }
+            if (u >= nouter) break;
+            // the slow path: lane 0 polls for its input word u (bounded)
+            bool lok = true;
+            if (lane == 0) in0 = poll_global_lane(src_row + u, epoch, P.err, P.wait_limit_ns, lok);
+            if (!__all_sync(kFull, lok)) {
+                ok = false;
+                break;
             }
         }
         asm volatile("cp.async.wait_all;" ::: "memory");
@@ -352,13 +370,11 @@ static __device__ __forceinline__ void batch_job(const BatchArgs &P, const SegJo
 template <bool TILES>
 __global__ void __launch_bounds__(32) k_batch(const BatchArgs P) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ __align__(16) uint64_t s_src[2 * kBatchSrcRing];
     __shared__ __align__(16) uint32_t s_cols[(kColRing + 2) * 32];
     const int lane = threadIdx.x & 31;
     uint32_t *pm = reinterpret_cast<uint32_t *>(smem);
     const uint32_t pm_lane = (uint32_t)__cvta_generic_to_shared(pm + lane);
     const uint32_t col_ring = (uint32_t)__cvta_generic_to_shared(s_cols);
-    const uint32_t src_ring = (uint32_t)__cvta_generic_to_shared(s_src);
     for (int c = 0; c < P.table_rows; ++c) pm[c * 32 + lane] = 0u;
     for (int i = lane; i < (kColRing + 2) * 32; i += 32) s_cols[i] = 0u;  // valid offsets from the start
     const uint32_t epoch = *P.epoch_dev;
@@ -374,9 +390,9 @@ __global__ void __launch_bounds__(32) k_batch(const BatchArgs P) {
         // the chunk width of the job's size class
         const int cl = (int)((J.flags >> kClassShift) & 3u);  // (no dynamic index into the parameters)
         const int C = cl == 0 ? P.cls_chunk[0] : (cl == 1 ? P.cls_chunk[1] : (cl == 2 ? P.cls_chunk[2] : P.cls_chunk[3]));
-        if (C == 2) batch_job<2, TILES>(P, J, lane, pm, pm_lane, s_cols, col_ring, src_ring, epoch);
-        else if (C == 4) batch_job<4, TILES>(P, J, lane, pm, pm_lane, s_cols, col_ring, src_ring, epoch);
-        else batch_job<8, TILES>(P, J, lane, pm, pm_lane, s_cols, col_ring, src_ring, epoch);
+        if (C == 2) batch_job<2, TILES>(P, J, lane, pm, pm_lane, s_cols, col_ring, epoch);
+        else if (C == 4) batch_job<4, TILES>(P, J, lane, pm, pm_lane, s_cols, col_ring, epoch);
+        else batch_job<8, TILES>(P, J, lane, pm, pm_lane, s_cols, col_ring, epoch);
     }
 }
 
