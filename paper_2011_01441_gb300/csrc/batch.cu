@@ -5,8 +5,9 @@
 // rows are cut into segments of at most 32 lanes x 31 rows, each segment is
 // one warp job that streams all columns of the pair; a pair taller than one
 // warp chains its segments through epoch-tagged carry words in global memory
-// (the same hand-off the single-pair strips use).  Jobs are ordered largest
-// pair first (LPT), so the persistent warps, which take jobs from one atomic
+// (the same hand-off the single-pair strips use).  Jobs are ordered by the
+// length of the segment chain they start (critical path first, then the
+// largest pair), so the persistent warps, which take jobs from one atomic
 // ticket, end together: this is the balanced share of cells per SM the PACO
 // partition asks for, here over independent pairs instead of one table.
 #include "../../include/paco_lcs.h"
@@ -157,8 +158,7 @@ constexpr int kColRing = 32;
 constexpr int kColAhead = 8;
 
 // One warp job (a segment of up to 32 lanes x 31 rows of one pair, all its
-// columns) with chunk width C.  The pipeline ends at the segment's last
-// real lane: that lane hands the bottom row on.
+// columns) with chunk width C.  Lane 31 hands the bottom row on.
 template <int C, bool TILES>
 static __device__ __forceinline__ void batch_job(const BatchArgs &P, const SegJob &J, const int lane, uint32_t *pm,
                                                  const uint32_t pm_lane, uint32_t *cols_ptr, const uint32_t col_ring,
@@ -205,11 +205,19 @@ static __device__ __forceinline__ void batch_job(const BatchArgs &P, const SegJo
         // the job's scalars, broadcast from lane 0 so the compiler sees them
         // as warp-uniform (uniform branches, no reconvergence barriers)
         const int nwords = __shfl_sync(kFull, (int)((S + 31) >> 5), 0);
-        const int last = __shfl_sync(kFull, (J.nrows - 1) / kLaneRows, 0);  // last real lane: the pipeline's end
-        const int flush_i = (last + K - 1) % K;         // step at which it completes a word
-        // words lane 0 runs over: the real ones, then zero-row words until the
-        // last lane has finished the last real word
-        const int nouter = (nwords * K + last + K - 1) / K;
+        // The pipeline always runs through lane 31: lanes past the segment's
+        // rows hold no rows (zero match words, every vertical step 1), so they
+        // pass each carry on unchanged and lane 31 emits the segment's bottom
+        // row a few steps later.  The step at which it completes a word is
+        // then the same for every job (no per-step test): at step i of word
+        // u, lane 31 ends column 32 u + (i - 30) C - 1, the last column of
+        // word u - kFlushLag when i = kFlushI.
+        constexpr int kFlushI = 30 % K;
+        constexpr int kFlushLag = (30 - kFlushI) / K + 1;
+        static_assert((30 - kFlushI) % K == 0, "lane 31 ends a word at step kFlushI");
+        // words lane 0 runs over: the real ones, then zero-row words until
+        // lane 31 has finished the last real word
+        const int nouter = nwords + (31 + K - 1) / K;
         const bool in_global = __shfl_sync(kFull, (J.flags & kInGlobal) != 0 ? 1 : 0, 0) != 0;
         const bool out_global = __shfl_sync(kFull, (J.flags & kOutGlobal) != 0 ? 1 : 0, 0) != 0;
         const uint64_t *src_row = P.hbuf + J.hin;
@@ -219,7 +227,7 @@ static __device__ __forceinline__ void batch_job(const BatchArgs &P, const SegJo
 
         uint32_t cw = 0;      // this lane's carry-outs, newest in bit 0 (never reset)
         uint32_t sr = 0;      // carry-ins, next one in bit 31
-        uint32_t total = 0;   // the last lane of a final segment: set bits of the bottom row
+        uint32_t total = 0;   // lane 31 of a final segment: set bits of the bottom row
         bool ok = true;
         // lanes 0..7 copy one 32-column word (16 bytes each); lanes 8..15 the
         // mirror copy when the word lands in slot 0 or 1.  Columns at or past
@@ -302,7 +310,6 @@ static __device__ __forceinline__ void batch_job(const BatchArgs &P, const SegJo
                 in0 = in1;
                 if (in_global && u + 2 < nwords) in1 = ld_relaxed_u64(src_row + u + 2);
                 if (lane == 0) sr = srcw;
-                const int ubase = u * K;
                 // this lane's column of step 0 (lane k trails lane 0 by k chunks) in the ring
                 const int c0 = u * 32 - C * lane;
                 const uint32_t cbase = col_ring + (uint32_t)(((c0 >> 5) & (kColRing - 1)) * 128) + (uint32_t)((c0 & 31) * 4);
@@ -324,9 +331,9 @@ static __device__ __forceinline__ void batch_job(const BatchArgs &P, const SegJo
                         Mcur[jj] = Mnext[jj];
                         onext[jj] = onext2[jj];
                     }
-                    if (i == flush_i) {  // the last lane completes word wq (predicated stores)
-                        const int wq = ((ubase + i - last) * C) >> 5;
-                        const bool fl = lane == last && wq >= 0 && wq < nwords;
+                    if (i == kFlushI) {  // lane 31 completes word wq (predicated stores)
+                        const int wq = u - kFlushLag;
+                        const bool fl = lane == 31 && wq >= 0 && wq < nwords;
                         st_relaxed_u64_if(fl && out_global, dst_row + (fl ? wq : 0), ((uint64_t)epoch << 32) | cw);
                         total += (fl && !out_global) ? (uint32_t)__popc(cw) : 0u;
                         st_u32_if(fl && keep_bits, bout + (fl ? wq : 0), cw);
@@ -345,7 +352,7 @@ static __device__ __forceinline__ void batch_job(const BatchArgs &P, const SegJo
         asm volatile("cp.async.wait_all;" ::: "memory");
         __syncwarp();
 
-        if (ok && lane == last && (J.flags & kFinal)) P.len[J.pair] = (int32_t)total;
+        if (ok && lane == 31 && (J.flags & kFinal)) P.len[J.pair] = (int32_t)total;
         if (ok && J.rword >= 0 && nreal > 0) P.rbits[J.rword + lane] = ~V & realmask;
         if (TILES && (J.flags & kRightOut) && nreal > 0)
             st_relaxed_u64_if(true, P.vbuf + J.vout + lane, ((uint64_t)epoch << 32) | V);
@@ -522,8 +529,14 @@ struct Layout {
     int64_t cells = 0;
 };
 
-// Segments, carry rows and output word offsets for a batch; jobs in LPT
-// order (largest L*S first), the segments of a pair consecutive.
+// Segments, carry rows and output word offsets for a batch.  Jobs run in
+// critical-path order: a segment's priority is the length of the chain that
+// starts with it, S columns plus one pipeline fill (the lanes' skew and one
+// word, about 31 C + 32 columns at C = 4) for every segment below it.  A
+// pair's segments keep their order (each comes after the one above it, so
+// a warp only ever waits for a running segment), and a tall, narrow pair,
+// whose chain is long for its few cells, starts early instead of last.
+constexpr int64_t kChainFill = 31 * 4 + 32;
 void plan_batch(int32_t npairs, const int64_t *a_off, const int64_t *b_off, bool want_rows,
                 bool want_cols, const int64_t *row_off, const int64_t *col_off, Layout &lay) {
     lay = Layout();
@@ -535,6 +548,7 @@ void plan_batch(int32_t npairs, const int64_t *a_off, const int64_t *b_off, bool
     std::stable_sort(order.begin(), order.end(),
                      [&](int32_t x, int32_t y) { return work[(size_t)x] > work[(size_t)y]; });
     const int64_t seg_rows = 32 * 31;
+    std::vector<int64_t> prio;  // per job, in the order built
     for (int32_t k : order) {
         const int64_t n = a_off[k + 1] - a_off[k], m = b_off[k + 1] - b_off[k];
         const bool tr = m > n;
@@ -601,10 +615,18 @@ void plan_batch(int32_t npairs, const int64_t *a_off, const int64_t *b_off, bool
             if (J.flags & kFinal) J.bword = pj.bword;
             else J.bword = -1;
             lay.jobs.push_back(J);
+            prio.push_back(S + kChainFill * (nseg - j));
             ++lay.class_jobs[size_class(S)];
         }
         if (want_rows || want_cols) lay.pjobs.push_back(pj);
     }
+    std::vector<int64_t> idx(lay.jobs.size());
+    std::iota(idx.begin(), idx.end(), (int64_t)0);
+    std::stable_sort(idx.begin(), idx.end(), [&](int64_t x, int64_t y) { return prio[(size_t)x] > prio[(size_t)y]; });
+    std::vector<SegJob> sorted;
+    sorted.reserve(lay.jobs.size());
+    for (int64_t i : idx) sorted.push_back(lay.jobs[(size_t)i]);
+    lay.jobs.swap(sorted);
 }
 
 uint64_t fnv(const void *p, size_t n, uint64_t h = 1469598103934665603ull) {
