@@ -228,7 +228,7 @@ static __device__ __forceinline__ void flush_out(const AffArgs &P, const AffJob 
     }
 }
 
-template <int R, int KL>
+template <int R, int KL, bool PAIR>
 static __device__ __forceinline__ void affine_band(const AffArgs &P, const AffJob &J, int jid, int4 (*stage)[kAffChunk],
                                                    int2 *sout) {
     const int lane = threadIdx.x & 31;
@@ -265,7 +265,16 @@ static __device__ __forceinline__ void affine_band(const AffArgs &P, const AffJo
 
     const int T = m + nr;              // steps: the last row reaches column m at T - 1
     const int hot = (m / kAffChunk) * kAffChunk;   // steps before `hot` never reach column m
-    for (int c = 0; c * kAffChunk < hot; ++c) {
+    // Every chunk runs as one block of 32 steps (unrolled), the chunks from
+    // `hot` on with the capture of column m (the right column).  The steps
+    // of the last chunk past T - 1 touch only cells beyond the table, which
+    // nothing reads.  The band below waits for this band's last chunk, so a
+    // slow tail here would delay every band after it.  A single pair's chain
+    // runs one band per warp scheduler and takes the fully unrolled block; a
+    // batch, with many warps per SM running different bands, takes blocks
+    // half as long (less code for the instruction cache to hold).
+    const int nchunks = (T + kAffChunk - 1) / kAffChunk;
+    for (int c = 0; c < nchunks; ++c) {
         if (c > 0) {
             GATHER();
             flush_out(P, J, o, lane, (c - 1) * kAffChunk, T, out);
@@ -277,30 +286,23 @@ static __device__ __forceinline__ void affine_band(const AffArgs &P, const AffJo
             __syncwarp();
         }
         const int4 *st = stage[c & 1];
-#pragma unroll
-        for (int u = 0; u < kAffChunk; ++u) {
-            band_step<R, false>(S, st[u], c * kAffChunk + u, lane, m, gm, gx, ge, goe);
-            COLLECT(u);
+        const int t0 = c * kAffChunk;
+        if (t0 < hot) {
+#pragma unroll(PAIR ? kAffChunk : kAffChunk / 2)
+            for (int u = 0; u < kAffChunk; ++u) {
+                band_step<R, false>(S, st[u], t0 + u, lane, m, gm, gx, ge, goe);
+                COLLECT(u);
+            }
+        } else {
+#pragma unroll 4
+            for (int u = 0; u < kAffChunk; ++u) {
+                band_step<R, true>(S, st[u], t0 + u, lane, m, gm, gx, ge, goe);
+                COLLECT(u);
+            }
         }
-    }
-    for (int t = hot; t < T; ++t) {
-        const int u = t % kAffChunk;
-        if (u == 0 && t > 0) {
-            GATHER();
-            flush_out(P, J, o, lane, t - kAffChunk, T, out);
-            const int c = t / kAffChunk;
-            const int col = c * kAffChunk + lane;
-            if (!settle_chunk(P, J, col, cur, want)) return;
-            __syncwarp();
-            if (lane < kAffChunk) stage[c & 1][lane] = band_input(P, J, col, cur);
-            cur = load_chunk(P, J, col + kAffChunk);
-            __syncwarp();
-        }
-        band_step<R, true>(S, stage[(t / kAffChunk) & 1][u], t, lane, m, gm, gx, ge, goe);
-        COLLECT(u);
     }
     GATHER();
-    flush_out(P, J, o, lane, ((T - 1) / kAffChunk) * kAffChunk, T, out);
+    flush_out(P, J, o, lane, (nchunks - 1) * kAffChunk, T, out);
 #undef COLLECT
 #undef GATHER
     if (P.right_col) {
@@ -314,7 +316,7 @@ static __device__ __forceinline__ void affine_band(const AffArgs &P, const AffJo
     }
 }
 
-template <int R>
+template <int R, bool PAIR>
 __global__ void __launch_bounds__(32 * kAffWarps) k_affine(AffArgs P) {
     __shared__ int4 stage[kAffWarps][2][kAffChunk];
     __shared__ int2 sout[kAffWarps][kAffChunk];
@@ -326,14 +328,14 @@ __global__ void __launch_bounds__(32 * kAffWarps) k_affine(AffArgs P) {
         if (jid >= P.njobs) return;
         const AffJob J = P.jobs[jid];
         switch ((J.nr - 1) % R) {
-            case 0: affine_band<R, 0>(P, J, jid, stage[w], sout[w]); break;
-            case 1: affine_band<R, 1>(P, J, jid, stage[w], sout[w]); break;
-            case 2: if (R > 2) affine_band<R, (R > 2 ? 2 : 0)>(P, J, jid, stage[w], sout[w]); break;
-            case 3: if (R > 3) affine_band<R, (R > 3 ? 3 : 0)>(P, J, jid, stage[w], sout[w]); break;
-            case 4: if (R > 4) affine_band<R, (R > 4 ? 4 : 0)>(P, J, jid, stage[w], sout[w]); break;
-            case 5: if (R > 5) affine_band<R, (R > 5 ? 5 : 0)>(P, J, jid, stage[w], sout[w]); break;
-            case 6: if (R > 6) affine_band<R, (R > 6 ? 6 : 0)>(P, J, jid, stage[w], sout[w]); break;
-            case 7: if (R > 7) affine_band<R, (R > 7 ? 7 : 0)>(P, J, jid, stage[w], sout[w]); break;
+            case 0: affine_band<R, 0, PAIR>(P, J, jid, stage[w], sout[w]); break;
+            case 1: affine_band<R, 1, PAIR>(P, J, jid, stage[w], sout[w]); break;
+            case 2: if (R > 2) affine_band<R, (R > 2 ? 2 : 0), PAIR>(P, J, jid, stage[w], sout[w]); break;
+            case 3: if (R > 3) affine_band<R, (R > 3 ? 3 : 0), PAIR>(P, J, jid, stage[w], sout[w]); break;
+            case 4: if (R > 4) affine_band<R, (R > 4 ? 4 : 0), PAIR>(P, J, jid, stage[w], sout[w]); break;
+            case 5: if (R > 5) affine_band<R, (R > 5 ? 5 : 0), PAIR>(P, J, jid, stage[w], sout[w]); break;
+            case 6: if (R > 6) affine_band<R, (R > 6 ? 6 : 0), PAIR>(P, J, jid, stage[w], sout[w]); break;
+            case 7: if (R > 7) affine_band<R, (R > 7 ? 7 : 0), PAIR>(P, J, jid, stage[w], sout[w]); break;
         }
     }
 }
@@ -356,9 +358,9 @@ __global__ void k_affine_degenerate(const int32_t *pairs, int count, const int64
 
 int aff_occupancy(int R) {
     int blocks = 0;
-    cudaError_t e = R == 8   ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_affine<8>, 32 * kAffWarps, 0)
-                    : R == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_affine<2>, 32 * kAffWarps, 0)
-                             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_affine<4>, 32 * kAffWarps, 0);
+    cudaError_t e = R == 8   ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_affine<8, false>, 32 * kAffWarps, 0)
+                    : R == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_affine<2, false>, 32 * kAffWarps, 0)
+                             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_affine<4, false>, 32 * kAffWarps, 0);
     return e == cudaSuccess ? std::max(blocks, 1) : 1;
 }
 
@@ -525,9 +527,10 @@ static int run_affine(paco_ctx *ctx, const uint8_t *a_cat, const int64_t *h_a_of
         const int per_sm = npairs == 1 ? 1 : aff_occupancy(R);
         const int grid = std::min(ctx->sms * per_sm, (njobs + kAffWarps - 1) / kAffWarps);
         cudaEventRecord(ctx->ev0, st);
-        if (R == 8) k_affine<8><<<grid, 32 * kAffWarps, 0, st>>>(P);
-        else if (R == 2) k_affine<2><<<grid, 32 * kAffWarps, 0, st>>>(P);
-        else k_affine<4><<<grid, 32 * kAffWarps, 0, st>>>(P);
+        const bool pair = npairs == 1;
+        if (R == 8) pair ? k_affine<8, true><<<grid, 32 * kAffWarps, 0, st>>>(P) : k_affine<8, false><<<grid, 32 * kAffWarps, 0, st>>>(P);
+        else if (R == 2) pair ? k_affine<2, true><<<grid, 32 * kAffWarps, 0, st>>>(P) : k_affine<2, false><<<grid, 32 * kAffWarps, 0, st>>>(P);
+        else pair ? k_affine<4, true><<<grid, 32 * kAffWarps, 0, st>>>(P) : k_affine<4, false><<<grid, 32 * kAffWarps, 0, st>>>(P);
         e = cudaGetLastError();
         cudaEventRecord(ctx->ev1, st);
         if (e != cudaSuccess) return set_cuda_error(ctx, e, "k_affine");
