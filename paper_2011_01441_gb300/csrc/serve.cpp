@@ -2,7 +2,8 @@
 //
 // paco_lcs_submit copies a request's strings into pinned host arenas (one
 // for the a strings, one for the b strings, each a FIFO ring) and returns a
-// ticket.  One worker thread per stream slot (kStreams of them) admits queued
+// ticket (paco_lcs_submit_many copies a large submission's strings with a
+// few helper threads).  One worker thread per stream slot (kStreams of them) admits queued
 // requests while the device budget allows, packs them into a micro-batch and
 // launches it (the batch engine, one persistent launch) on its slot's
 // stream, so micro-batches overlap on the device and their host preparation
@@ -18,6 +19,7 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -35,10 +37,14 @@ namespace {
 constexpr int kStreams = 8;
 constexpr size_t kMaxQueued = 1u << 20;
 constexpr int32_t kMaxBatchPairs = 8192;
-// Up to ~0.5 ms of device work per micro-batch at the batch kernel's rate:
-// small enough for several to overlap, large enough to amortise each
-// micro-batch's host work (layout, copies, launches).
-constexpr int64_t kMaxBatchCells = 20000000000LL;
+// Up to ~2.5 ms of device work per micro-batch at the batch kernel's rate on
+// the serving mix.  A micro-batch lasts at least as long as its longest
+// chain of segments (a tall pair), so small ones leave the device idle
+// around that chain: on the 100k-request serving mix, caps of 2e10 / 6e10 /
+// 2e11 cells served 52 / 62 / 64 TCUPS at the saturating rate, with lower
+// latency too (p99 at 0.9 of it 40 / 27 / 26 ms).  Under light load the cap
+// does not bind: a worker takes what has arrived.
+constexpr int64_t kMaxBatchCells = 200000000000LL;
 // Pinned arena per string side (a, b).
 constexpr size_t kArenaBytes = (size_t)256 << 20;
 
@@ -103,6 +109,82 @@ struct Slot {
     uint64_t seq = 0;  // admission number of the micro-batch (arena reclaim order)
 };
 
+// The string copies of a large submission.  Copying the strings into the
+// pinned arenas is the ingest path's main cost (one core copies about
+// 10 GB/s, which capped serving near 600k requests/s on the serving mix), so
+// a submission of many bytes is copied by the submitting thread and
+// kCopyThreads helpers together, in pieces of at most kCopyPiece bytes taken
+// from one atomic counter.
+constexpr int kCopyThreads = 3;
+constexpr size_t kCopyPiece = (size_t)1 << 20;
+constexpr size_t kCopyParallelMin = (size_t)4 << 20;  // smaller submissions copy on the caller's thread
+constexpr int64_t kSubmitGroup = 512;                  // requests published together (workers start early)
+
+struct CopyPiece {
+    uint8_t *dst;
+    const uint8_t *src;
+    size_t n;
+};
+
+struct CopyPool {
+    std::mutex mu;
+    std::condition_variable cv, done_cv;
+    std::thread th[kCopyThreads];
+    const std::vector<CopyPiece> *pieces = nullptr;
+    std::atomic<size_t> next{0};
+    int pending = 0;   // helpers still on the current generation
+    uint64_t gen = 0;
+    bool stop = false;
+    void work() {
+        const std::vector<CopyPiece> &p = *pieces;
+        for (;;) {
+            const size_t i = next.fetch_add(1, std::memory_order_relaxed);
+            if (i >= p.size()) break;
+            std::memcpy(p[i].dst, p[i].src, p[i].n);
+        }
+    }
+    void helper() {
+        uint64_t seen = 0;
+        for (;;) {
+            {
+                std::unique_lock<std::mutex> lk(mu);
+                cv.wait(lk, [&] { return stop || gen != seen; });
+                if (stop) return;
+                seen = gen;
+            }
+            work();
+            std::lock_guard<std::mutex> lk(mu);
+            if (--pending == 0) done_cv.notify_all();
+        }
+    }
+    void start() {
+        for (auto &t : th) t = std::thread(&CopyPool::helper, this);
+    }
+    void run(const std::vector<CopyPiece> &p) {  // the caller copies too; returns when every piece is done
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            pieces = &p;
+            next.store(0, std::memory_order_relaxed);
+            pending = kCopyThreads;
+            ++gen;
+        }
+        cv.notify_all();
+        work();
+        std::unique_lock<std::mutex> lk(mu);
+        done_cv.wait(lk, [&] { return pending == 0; });
+        pieces = nullptr;
+    }
+    void shutdown() {
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            stop = true;
+        }
+        cv.notify_all();
+        for (auto &t : th)
+            if (t.joinable()) t.join();
+    }
+};
+
 // Arena space of one admitted micro-batch, reclaimed in admission order.
 struct Held {
     uint64_t seq, a_end, b_end;
@@ -141,6 +223,7 @@ struct ServeEngine {
     bool stop = false;
     std::thread workers[kStreams];
     Slot slots[kStreams];
+    CopyPool copier;   // used under sub_mu
     paco_serve_stats stats{};
     int init_status = PACO_OK;
 };
@@ -403,6 +486,71 @@ int enqueue(ServeEngine *E, const uint8_t *a, int64_t n, const uint8_t *b, int64
     return PACO_OK;
 }
 
+// Queue requests k0 .. k1 - 1 of a concatenated submission (the caller holds
+// sub_mu): reserve arena space for as many as fit, copy their strings (in
+// parallel when there are many bytes), then publish them in ticket order in
+// one critical section.  Returns how many were queued; *rc = PACO_EBUSY when
+// an arena, the queue or the budget stopped it early.
+int64_t enqueue_group(ServeEngine *E, const uint8_t *a_cat, const int64_t *a_off, const uint8_t *b_cat,
+                      const int64_t *b_off, int64_t k0, int64_t k1, uint64_t *tickets, int *rc) {
+    Arena ta, tb;
+    size_t queued = 0;
+    {
+        std::lock_guard<std::mutex> lk(E->mu);
+        ta = E->arena_a;
+        tb = E->arena_b;
+        queued = E->queue.size();
+    }
+    std::vector<std::unique_ptr<Request>> reqs;
+    reqs.reserve((size_t)(k1 - k0));
+    std::vector<CopyPiece> pieces;
+    size_t total = 0;
+    auto add = [&](uint8_t *dst, const uint8_t *src, size_t n) {
+        for (size_t o = 0; o < n; o += kCopyPiece) pieces.push_back({dst + o, src + o, std::min(kCopyPiece, n - o)});
+        total += n;
+    };
+    for (int64_t k = k0; k < k1; ++k) {
+        const int64_t n = a_off[k + 1] - a_off[k], m = b_off[k + 1] - b_off[k];
+        const size_t bytes = request_bytes(n, m, false);
+        if (bytes > E->budget || (size_t)n > ta.cap || (size_t)m > tb.cap || queued + reqs.size() >= kMaxQueued) {
+            *rc = PACO_EBUSY;
+            break;
+        }
+        auto r = std::make_unique<Request>();
+        if (!ta.reserve(n, &r->a_pos) || !tb.reserve(m, &r->b_pos)) {
+            *rc = PACO_EBUSY;
+            break;
+        }
+        // the reserved bytes lie past every admitted request's, so no reader
+        // touches them until the request is queued
+        if (n) add(ta.at(r->a_pos), a_cat + a_off[k], (size_t)n);
+        if (m) add(tb.at(r->b_pos), b_cat + b_off[k], (size_t)m);
+        r->n = n;
+        r->m = m;
+        r->bytes = bytes;
+        reqs.push_back(std::move(r));
+    }
+    if (reqs.empty()) return 0;
+    if (total >= kCopyParallelMin) {
+        E->copier.run(pieces);
+    } else {
+        for (const CopyPiece &c : pieces) std::memcpy(c.dst, c.src, c.n);
+    }
+    std::lock_guard<std::mutex> lk(E->mu);
+    E->arena_a.head = ta.head;
+    E->arena_b.head = tb.head;
+    int64_t k = k0;
+    for (auto &r : reqs) {
+        r->ticket = E->next_ticket++;
+        tickets[k++] = r->ticket;
+        E->queue.push_back(r.get());
+        E->table.push_back(std::move(r));
+    }
+    E->stats.submitted += reqs.size();
+    E->stats.queued_now = E->queue.size();
+    return (int64_t)reqs.size();
+}
+
 }  // namespace
 
 ServeEngine *serve_get(paco_ctx *ctx, int *rc) {
@@ -447,6 +595,7 @@ ServeEngine *serve_get(paco_ctx *ctx, int *rc) {
         S.B = batch_state_new((int *)S.small.ptr, (int *)S.small.ptr + 1);
     }
     for (int k = 0; k < kStreams; ++k) E->workers[k] = std::thread(slot_main, E, k);
+    E->copier.start();
     *rc = PACO_OK;
     return E;
 }
@@ -461,6 +610,7 @@ void serve_shutdown(paco_ctx *ctx) {
     E->cv.notify_all();
     for (auto &t : E->workers)
         if (t.joinable()) t.join();
+    E->copier.shutdown();
     for (auto &S : E->slots) {
         if (S.stream) cudaStreamSynchronize(S.stream);
         batch_state_free(S.B);
@@ -521,12 +671,13 @@ int paco_lcs_submit_many(paco_ctx *ctx, const uint8_t *a_cat, const int64_t *a_o
     int64_t taken = 0;
     {
         std::lock_guard<std::mutex> lk(E->sub_mu);
-        for (int64_t k = 0; k < count; ++k) {
-            const int64_t n = a_off[k + 1] - a_off[k], m = b_off[k + 1] - b_off[k];
-            rc = paco::enqueue(E, a_cat + a_off[k], n, b_cat + b_off[k], m, false, &tickets[k]);
-            if (rc != PACO_OK) break;
-            ++taken;
-            if ((taken & 63) == 0) E->cv.notify_one();  // let a worker start on a long submission
+        while (taken < count && rc == PACO_OK) {
+            const int64_t k1 = std::min(count, taken + paco::kSubmitGroup);
+            const int64_t got = paco::enqueue_group(E, a_cat, a_off, b_cat, b_off, taken, k1, tickets, &rc);
+            if (got) E->cv.notify_one();  // let a worker start on a long submission
+            const bool partial = taken + got < k1;
+            taken += got;
+            if (partial) break;
         }
     }
     if (n_submitted) *n_submitted = taken;
