@@ -256,7 +256,9 @@ int grow_dev(DevBuf &d, size_t need, cudaStream_t st) {
 }
 
 // One side's strings of a micro-batch to the device: the runs of requests
-// whose strings follow each other in the arena, one copy per run.
+// whose strings follow each other in the arena, one copy per run.  A run
+// ends at the arena's physical end: a string that starts a new lap at
+// offset 0 follows the previous one logically but not in memory.
 cudaError_t copy_side(Arena &ar, const std::vector<Request *> &reqs, bool side_a, uint8_t *dst, cudaStream_t st) {
     size_t k = 0, out = 0;
     while (k < reqs.size()) {
@@ -266,7 +268,7 @@ cudaError_t copy_side(Arena &ar, const std::vector<Request *> &reqs, bool side_a
         while (j < reqs.size()) {
             const uint64_t p = side_a ? reqs[j]->a_pos : reqs[j]->b_pos;
             const int64_t len = side_a ? reqs[j]->n : reqs[j]->m;
-            if (p != end) break;
+            if (p != end || (j > k && p % ar.cap == 0)) break;
             end = p + (uint64_t)len;
             ++j;
         }

@@ -308,3 +308,46 @@ def test_serve_arena_laps_and_full_arena(ctx):
     for j in range(k_total):
         want = 1 if (j % 5 == 0 and j % 4 == 0) else 0
         assert got[j] == want, (j, got[j])
+
+
+def test_serve_one_large_submission_in_groups(ctx):
+    """One submit_many call of 600 requests with 1 MiB a-strings (600 MiB,
+    more than the 256 MiB a-arena): the strings are copied by the submitting
+    thread and its helpers, the call takes the requests that fit and stops
+    with PACO_EBUSY partway through its first group of 512, and the rest goes
+    in as arena space comes back.  b is one symbol, so L = 1 exactly when a
+    holds it."""
+    k_total = 600
+    n = 1 << 20
+    a_cat = np.empty(k_total * n, np.uint8)
+    for j in range(k_total):
+        a_cat[j * n:(j + 1) * n] = j % 3
+        a_cat[j * n + (j * 977) % n] = 9 if j % 4 == 0 else 1  # a holds 9 only when j % 4 == 0
+    a_off = np.arange(k_total + 1, dtype=np.int64) * n
+    b_cat = np.array([9 if j % 5 == 0 else 3 for j in range(k_total)], np.uint8)
+    b_off = np.arange(k_total + 1, dtype=np.int64)
+    pending, got, k = {}, {}, 0
+    first = None
+    t0 = time.time()
+    while len(got) < k_total:
+        assert time.time() - t0 < 300
+        if k < k_total:
+            t = P.paco_lcs_submit_many(ctx, a_cat[a_off[k]:], a_off[k:] - a_off[k], b_cat[k:], b_off[k:] - b_off[k],
+                                       partial=True)
+            if first is None:
+                first = t.size
+            for i, ticket in enumerate(t):
+                pending[int(ticket)] = k + i
+            k += t.size
+        if pending:
+            tick = np.array(list(pending), np.uint64)
+            st, ln = P.paco_lcs_poll_many(ctx, tick)
+            for ticket, s_, l_ in zip(tick, st, ln):
+                if s_ != P.PACO_PENDING:
+                    assert s_ == P.PACO_OK
+                    got[pending.pop(int(ticket))] = int(l_)
+        time.sleep(0.001)
+    assert 0 < first < 512  # stopped by the full arena inside the first group
+    for j in range(k_total):
+        want = 1 if (j % 5 == 0 and j % 4 == 0) else 0
+        assert got[j] == want, (j, got[j])
