@@ -116,6 +116,23 @@ def test_batch_tall_pairs_chain_segments(ctx):
     check_batch(ctx, B, A, boundaries=True)
 
 
+@pytest.mark.parametrize("chunk", [0, 2, 8])
+def test_batch_tall_narrow_chains_among_square_pairs(ctx, chunk):
+    """Pairs of 20000-30000 rows and 1-64 columns (chains of 21-31 segments
+    with one or two words each, started early by the critical-path order and
+    interleaved with other pairs' segments) mixed with square pairs, both
+    orientations, with both boundaries."""
+    A, B = [], []
+    for k, (n, m) in enumerate([(30000, 1), (20000, 2), (25000, 31), (22000, 33), (30000, 64), (3000, 2900),
+                                (1500, 1500), (993, 992), (40, 20000)]):
+        a = W.symbols(97, k, n, 4)
+        b = W.symbols(98, k, m, 4)
+        A.append(a)
+        B.append(b)
+    check_batch(ctx, A, B, boundaries=True, chunk=chunk)
+    check_batch(ctx, B, A, boundaries=True, chunk=chunk)
+
+
 def test_batch_declared_alphabet(ctx):
     """A declared alphabet shrinks the match table; results are unchanged,
     and a symbol outside it is reported (PACO_EINVAL) without a fault."""
