@@ -3,11 +3,11 @@
 // paco_lcs_submit copies a request's strings into pinned host arenas (one
 // for the a strings, one for the b strings, each a FIFO ring) and returns a
 // ticket (paco_lcs_submit_many copies a large submission's strings with a
-// few helper threads).  One worker thread per stream slot (kStreams of them) admits queued
-// requests while the device budget allows, packs them into a micro-batch and
-// launches it (the batch engine, one persistent launch) on its slot's
-// stream, so micro-batches overlap on the device and their host preparation
-// runs in parallel.  Requests are admitted in submission order, so a
+// few helper threads).  One worker thread per stream slot (kStreams of them)
+// admits queued requests while the device budget allows, packs them into a
+// micro-batch and launches it (the batch engine, one persistent launch) on
+// its slot's stream, so micro-batches overlap on the device and their host
+// preparation runs in parallel.  Requests are admitted in submission order, so a
 // micro-batch's strings are one or two contiguous runs of each arena and go
 // to the device in as many copies, straight from where submit put them.
 // When a micro-batch's completion event fires its results are copied into
