@@ -14,10 +14,10 @@
 // (every job after the jobs it waits for, so a job only ever waits for a
 // running or finished one; the order is computed from the ticket number).
 // S(a, b) folds min_i D[i] + w(i, j) over block a into block b's running
-// minima P[j] with atomicMin and counts itself done.  T(b) waits for its
-// b - 1 squares, folds block b - 1 in itself 32 values at a time as they are
-// finished (so that square overlaps T(b - 1)), then solves its diagonal
-// triangle 32 values at a time: warp s finishes its values by a sequential
+// minima P[j] with atomicMin and counts itself done.  T(b) folds block b - 1
+// in itself 32 values at a time as they are finished (so that square
+// overlaps T(b - 1)), then waits for its b - 1 squares and takes their
+// minima, then solves its diagonal triangle 32 values at a time: warp s finishes its values by a sequential
 // sweep in which every lane carries the chain D[k] -> D[k+1] itself (the
 // running minimum of lane k + 1 is shuffled a step early), and the later
 // warps fold those 32 values in before their own turn.  Finished values are
@@ -304,12 +304,7 @@ __global__ void __launch_bounds__(kLwsBlock, 3) k_lws(LwsArgs P) {
                 sw[32 * 32 + k * 32 + lane] = lws_w(ib - 32 + k, jt, js, P.noise_mask);
             }
         }
-        // the squares (a, b), a < b - 1, are in P once all have counted
         int best = j == 0 ? P.d0 : kLwsInf;
-        if (b >= 2) {
-            if (!wait_count(P.done + b, b - 1, P.err, P.wait_limit_ns, &s_bad)) return;
-            if (j64 <= P.n) best = ld_relaxed_l2(P.P + j64);
-        }
         int *bz = P.busy + (smid() & (kLwsMaxSms - 1));
         if (t == 0) atomicAdd(bz, 1);
         // square (b - 1, b), 32 values at a time as T(b - 1) finishes them;
@@ -329,6 +324,17 @@ __global__ void __launch_bounds__(kLwsBlock, 3) k_lws(LwsArgs P) {
                 if (s + 1 < kLwsWarps && t < 32) pre = dev::ld_relaxed_u64(P.hand + h0 + 32 * (s + 1) + t);
                 best = fold_tile<false, 32>(best, sv, i0, jt, js, P.noise_mask);
             }
+        }
+        // then the squares (a, b), a < b - 1, which are in P once all have
+        // counted: waiting for them only after block b - 1 is folded keeps that
+        // fold overlapped with T(b - 1) (the square (b - 2, b) starts only when
+        // block b - 2 is final, and often ends after T(b - 1) does)
+        if (b >= 2) {
+            if (!wait_count(P.done + b, b - 1, P.err, P.wait_limit_ns, &s_bad)) {
+                if (t == 0) atomicSub(bz, 1);
+                return;
+            }
+            if (j64 <= P.n) best = min(best, ld_relaxed_l2(P.P + j64));
         }
 
         // the diagonal triangle of block b, 32 values at a time
