@@ -536,7 +536,13 @@ __global__ void __launch_bounds__(256, 1) k_pair_bp(const PairArgs P) {
                 }
             }
             bool stop = false;  // the next word lacks something
-#pragma unroll 2
+            // Words per iteration: a multiple of K steps that is also one of
+            // the carry queue's kQ entries, so the queue's rotation ends where
+            // it started and the loop's back edge moves no registers (with one
+            // word per lane, kQ = 3: three words ran the 131072 pair 3% faster
+            // than two; with two words per lane, kQ = 2 and two words stay
+            // best).
+#pragma unroll(kQ == 3 ? 3 : 2)
             for (; u < nouter;) {
                 // the input carry word u (its tag was checked)
                 const uint32_t srcw = u < nwords ? (uint32_t)in_next : 0u;
