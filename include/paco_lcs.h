@@ -244,7 +244,8 @@ int paco_lcs_batch(paco_ctx *ctx, const uint8_t *a_cat, const uint8_t *b_cat,
  * with whatever else is admitted, and is retrieved with paco_lcs_poll.
  * want_boundaries != 0 keeps bottom_row/right_col for poll.  Writes a ticket.
  * Errors: PACO_EINVAL, PACO_EBUSY (a single request larger than the budget,
- * or the host queue is full), PACO_ENOMEM. */
+ * or the host queue or string arena is full: retry after polling),
+ * PACO_ENOMEM. */
 int paco_lcs_submit(paco_ctx *ctx, const uint8_t *a, int64_t n,
                     const uint8_t *b, int64_t m, int want_boundaries,
                     uint64_t *ticket);
@@ -257,13 +258,17 @@ int paco_lcs_submit(paco_ctx *ctx, const uint8_t *a, int64_t n,
 int paco_lcs_poll(paco_ctx *ctx, uint64_t ticket, int32_t *len,
                   int32_t *row_out, int32_t *col_out);
 
-/* Submit `count` requests at once (one lock and one wake-up of the engine):
- * request k is a_cat[a_off[k] .. a_off[k+1]) against b_cat[b_off[k] ..
- * b_off[k+1]), all HOST buffers copied before the call returns; lengths only
- * (no boundaries).  tickets[count] receives the tickets.  Returns PACO_OK,
- * PACO_EINVAL for a bad argument (nothing submitted), or PACO_EBUSY when a
- * request does not fit the budget or the queue is full: then *n_submitted
- * (if not NULL) tells how many of the first requests were taken. */
+/* Submit `count` requests at once: request k is a_cat[a_off[k] ..
+ * a_off[k+1]) against b_cat[b_off[k] .. b_off[k+1]), all HOST buffers
+ * copied before the call returns (a submission of several MiB is copied by
+ * the calling thread and a few helper threads); lengths only (no
+ * boundaries).  Requests are published to the engine in groups of up to 512
+ * as their strings are copied, so the engine starts on the first group
+ * while later ones are copied.  tickets[count] receives the tickets.
+ * Returns PACO_OK, PACO_EINVAL for a bad argument (nothing submitted), or
+ * PACO_EBUSY when a request does not fit the budget, or the queue or string
+ * arena is full: then *n_submitted (if not NULL) tells how many of the
+ * first requests were taken, and the caller submits the rest after polling. */
 int paco_lcs_submit_many(paco_ctx *ctx, const uint8_t *a_cat, const int64_t *a_off,
                          const uint8_t *b_cat, const int64_t *b_off, int64_t count,
                          uint64_t *tickets, int64_t *n_submitted);
@@ -277,9 +282,9 @@ int paco_lcs_poll_many(paco_ctx *ctx, const uint64_t *tickets, int64_t count, in
 
 /* Serving statistics since the context was created: requests submitted and
  * completed, cells computed, queue and in-flight counts, micro-batches
- * launched, device bytes held and the budget, and the engine thread's host
- * time (ns) spent preparing and launching micro-batches and collecting
- * their results. */
+ * launched, device bytes held and the budget, and the worker threads' host
+ * time (ns, summed over the workers) spent preparing and launching
+ * micro-batches and collecting their results. */
 typedef struct paco_serve_stats {
     uint64_t submitted, completed, cells_done;
     uint64_t queued_now, inflight_now, batches_launched;
