@@ -127,3 +127,19 @@ def test_every_committed_summary_matches_its_kernel_source(bench_mod):
              "k_lws_n131072_full.md": ["lws.cu", "bp_device.cuh"]}
     for prof, srcs in cases.items():
         assert bench_mod._profiled_traffic(prof, srcs) is not None, prof
+
+
+def test_profile_commands_run_committed_files_only():
+    """Every ncu summary under profiles/ gives the command that made it, and
+    the scripts those commands run are files of this repository (bench.py,
+    or inline `python -c` code that imports the package)."""
+    import os
+    import re
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    pdir = os.path.join(root, "profiles")
+    for name in sorted(os.listdir(pdir)):
+        text = open(os.path.join(pdir, name)).read()
+        assert "ncu " in text and "--clock-control none" in text, name
+        for script in re.findall(r"python ([\w./-]+\.py)", text):
+            assert os.path.isfile(os.path.join(root, script)), (name, script)
+            assert not script.startswith("_work"), (name, script)
